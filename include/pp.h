@@ -1,0 +1,169 @@
+/*
+ * pp.h -- C ABI of the GB300 (sm_103a) particle-particle electron-bunch engine.
+ *
+ * The engine integrates the non-relativistic motion of N macro-electrons of
+ * weight w (charge q_e w, mass m_e w, q_e = -e) in open vacuum under their
+ * mutual Coulomb repulsion, following arXiv 2502.10640 Sec. 2.1:
+ *   - pair force, Eq. A, with r_ij = r_i - r_j;
+ *   - field at particle i from all j != i, Eq. B / Eq. E;
+ *   - acceleration a_i = (q_e/m_e) E_i, Eq. D / Eq. F (w cancels);
+ *   - Velocity Verlet, Eq. G (drift) and Eq. H (kick).
+ * An optional Plummer softening eps replaces |r|^2 by |r|^2 + eps^2 (eps = 0
+ * is Eq. A exactly).  A pair whose softened squared distance is zero adds
+ * nothing.  Pair arithmetic is FP32 on staged positions (re-centred and
+ * scaled by a power of two), accumulated per particle in FP64 (or in a
+ * compensated FP32 pair); positions, velocities and accelerations are FP64.
+ *
+ * Units are SI throughout: positions m, velocities m/s, accelerations m/s^2,
+ * fields V/m, energies J, momenta kg m/s, times s.
+ *
+ * Conventions for every call:
+ *   - Every call returns a pp_status.  On PP_ERR_ARG, PP_ERR_NOMEM,
+ *     PP_ERR_STATE and PP_ERR_TIMEOUT the context stays valid.  After
+ *     PP_ERR_CUDA the context must be destroyed.
+ *   - pp_last_error() gives a message for the last non-OK status returned
+ *     on the calling thread.
+ *   - Array arguments are [N][3] row-major doubles (x, y, z of particle i
+ *     at 3i, 3i+1, 3i+2).  on_device = 0: host memory (pageable or pinned);
+ *     on_device = 1: device memory of the context's GPU, read or written in
+ *     order on the context's stream.  Inputs are copied; the caller keeps
+ *     ownership of every buffer it passes.
+ *   - The library owns all device memory it allocates; pp_destroy frees it.
+ *   - Calls on one context must not run concurrently from several threads.
+ *   - Calls return after the work they enqueue has finished (the stream is
+ *     synchronised), so a status reflects device-side errors as well.
+ */
+#ifndef PP_GB300_H
+#define PP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_ctx pp_ctx;
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_ARG = -1,      /* invalid argument (size, pointer, non-finite value, option) */
+    PP_ERR_NOMEM = -2,    /* device allocation failed or a memory budget is exhausted    */
+    PP_ERR_CUDA = -3,     /* CUDA runtime error; destroy the context                      */
+    PP_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up; results of the call void */
+    PP_ERR_STATE = -5     /* call out of order (e.g. step before particles are loaded)    */
+} pp_status;
+
+/* Force accumulation modes (option PP_OPT_ACC). */
+typedef enum {
+    PP_ACC_FP64FOLD = 0,  /* FP32 pair math, FP32 tile partials folded into FP64 (default)  */
+    PP_ACC_KAHAN = 1,     /* FP32 pair math, tile partials folded into a compensated FP32 pair */
+    PP_ACC_FP64_FULL = 2  /* FP64 pair math and accumulation (comparison path, slow)        */
+} pp_acc;
+
+/* Option keys for pp_set_option. */
+enum {
+    PP_OPT_ACC = 1,            /* value: a pp_acc                                              */
+    PP_OPT_STREAM = 2,         /* value: cudaStream_t cast to int64 (0 = the context's own)   */
+    PP_OPT_SPLIT = 3,          /* value: j-split count S >= 1, or 0 for automatic              */
+    PP_OPT_GRAPH_BLOCK = 4,    /* value: steps per captured CUDA graph (0 = plain launches)   */
+    PP_OPT_TIMEOUT_NS = 5,     /* value: limit of each device-side wait in ns (default 1e9)   */
+    PP_OPT_VARIANT = 6,        /* value: force-kernel variant index (-1 = automatic)          */
+    PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy, so
+                                  its bounded waits expire and the call returns
+                                  PP_ERR_TIMEOUT (tests the timeout path; no fault, no hang) */
+};
+
+/*
+ * Create a context for N macro-electrons of common weight w (Sec. 2.1 assumes
+ * one weight for all macro-particles), time step dt > 0 and softening
+ * eps >= 0 (metres).  Allocates device memory on the current CUDA device.
+ * N >= 1 (N = 0 -> PP_ERR_ARG); N <= 2^28.  On success *out receives the
+ * context; on failure *out is set to NULL.
+ */
+pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **out);
+
+/* Set an option (keys above).  Invalid key or value -> PP_ERR_ARG. */
+pp_status pp_set_option(pp_ctx *ctx, int key, int64_t value);
+
+/*
+ * Load initial positions (m) and velocities (m/s), both [N][3].  vel may be
+ * NULL for a cold bunch (v = 0).  Non-finite entries -> PP_ERR_ARG.
+ * Computes the initial acceleration a(r0) (one force pass) so that the
+ * first pp_step applies Eq. G with it, and resets the step counter to 0.
+ */
+pp_status pp_load_particles(pp_ctx *ctx, const double *pos, const double *vel, int on_device);
+
+/*
+ * Field E_i (V/m) of Eq. B at every particle's current position, written as
+ * [N][3] to E_out.  Does not advance or modify the state.
+ */
+pp_status pp_compute_fields(pp_ctx *ctx, double *E_out, int on_device);
+
+/*
+ * Advance nsteps >= 0 Velocity-Verlet steps (Eq. G then Eq. H), one force
+ * pass per step.  Returns after the steps have run.  PP_ERR_STATE if no
+ * particles were loaded.
+ */
+pp_status pp_step(pp_ctx *ctx, int64_t nsteps);
+
+/* Bunch diagnostics; averages <.> are plain means over the N macro-particles. */
+typedef struct {
+    double t;           /* simulated time, step * dt                          */
+    int64_t step;       /* steps taken since the last load                    */
+    double rms_radius;  /* sqrt(<|r - <r>|^2>)                                */
+    double ke;          /* sum 1/2 m_e w |v|^2                                */
+    double pe;          /* 1/2 sum_i sum_{j!=i} k (q_e w)^2 / sqrt(|r_ij|^2+eps^2) */
+    double px, py, pz;  /* total momentum sum m_e w v                         */
+    double emit_x;      /* Eq. I with raw averages                            */
+    double x_rms;       /* sqrt(<x^2>)                                        */
+    double x_max;       /* max_i x_i                                          */
+    double vx_rms;      /* sqrt(<vx^2>)                                       */
+    double vx_max;      /* max_i vx_i                                         */
+    double cx, cy, cz;  /* centroid <r>                                       */
+} pp_diag;
+
+/*
+ * Diagnostics of the current state.  All moments are deterministic FP64
+ * reductions; pe needs one O(N^2) pass (FP32 pair math, FP64 fold).
+ * with_pe = 0 skips that pass and sets pe to NaN.
+ */
+pp_status pp_diagnostics(pp_ctx *ctx, pp_diag *out, int with_pe);
+
+/* Copy the current positions and velocities out ([N][3] each; either may be NULL). */
+pp_status pp_get_particles(pp_ctx *ctx, double *pos, double *vel, int on_device);
+
+/*
+ * Checkpoint / resume.  pp_get_state copies r, v, a ([N][3] each) and the
+ * step counter out; pp_set_state restores them exactly (no force pass), so
+ * that stepping on from a restored state is bitwise identical to stepping
+ * on without the round trip.  acc must be the acceleration that belongs to
+ * pos (as pp_get_state returns it).
+ */
+pp_status pp_get_state(pp_ctx *ctx, double *pos, double *vel, double *acc, int64_t *step,
+                       int on_device);
+pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const double *acc,
+                       int64_t step, int on_device);
+
+/* Number of particles of the context. */
+pp_status pp_get_n(const pp_ctx *ctx, int64_t *n);
+
+/* Free the context and its device memory.  NULL is accepted. */
+pp_status pp_destroy(pp_ctx *ctx);
+
+/* Message for the last non-OK status on this thread (ctx may be NULL). */
+const char *pp_last_error(const pp_ctx *ctx);
+
+/* Library version string. */
+const char *pp_version(void);
+
+/*
+ * Pair-interaction count of one step, N*N (the all-pairs convention used for
+ * throughput: pair-interactions per second).
+ */
+double pp_pairs_per_step(int64_t N);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_GB300_H */

@@ -1,0 +1,298 @@
+"""ctypes binding of the C ABI in include/pp.h (same function names).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.
+Arrays may be numpy arrays (host memory, on_device = 0) or CUDA torch tensors (device
+memory, on_device = 1); both must be float64 with shape [N][3].  Non-OK statuses raise
+PPError carrying the status and the library's message.  If the compiled library is
+missing and cannot be built, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PP_OK = 0
+PP_ERR_ARG = -1
+PP_ERR_NOMEM = -2
+PP_ERR_CUDA = -3
+PP_ERR_TIMEOUT = -4
+PP_ERR_STATE = -5
+STATUS_NAMES = {0: "PP_OK", -1: "PP_ERR_ARG", -2: "PP_ERR_NOMEM", -3: "PP_ERR_CUDA",
+                -4: "PP_ERR_TIMEOUT", -5: "PP_ERR_STATE"}
+
+PP_ACC_FP64FOLD = 0
+PP_ACC_KAHAN = 1
+PP_ACC_FP64_FULL = 2
+
+PP_OPT_ACC = 1
+PP_OPT_STREAM = 2
+PP_OPT_SPLIT = 3
+PP_OPT_GRAPH_BLOCK = 4
+PP_OPT_TIMEOUT_NS = 5
+PP_OPT_VARIANT = 6
+PP_OPT_TEST_SKIP_COPY = 99
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class pp_diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_int64),
+                ("rms_radius", ctypes.c_double), ("ke", ctypes.c_double), ("pe", ctypes.c_double),
+                ("px", ctypes.c_double), ("py", ctypes.c_double), ("pz", ctypes.c_double),
+                ("emit_x", ctypes.c_double), ("x_rms", ctypes.c_double),
+                ("x_max", ctypes.c_double), ("vx_rms", ctypes.c_double),
+                ("vx_max", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("cz", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_DP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_CTX = ctypes.c_void_p
+
+# (name, restype, argtypes) of every exported symbol declared in include/pp.h
+SIGNATURES = [
+    ("pp_create", ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(_CTX)]),
+    ("pp_set_option", ctypes.c_int, [_CTX, ctypes.c_int, _I64]),
+    ("pp_load_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
+    ("pp_compute_fields", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
+    ("pp_step", ctypes.c_int, [_CTX, _I64]),
+    ("pp_diagnostics", ctypes.c_int, [_CTX, ctypes.POINTER(pp_diag), ctypes.c_int]),
+    ("pp_get_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
+    ("pp_get_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, ctypes.POINTER(_I64), ctypes.c_int]),
+    ("pp_set_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, _I64, ctypes.c_int]),
+    ("pp_get_n", ctypes.c_int, [_CTX, ctypes.POINTER(_I64)]),
+    ("pp_destroy", ctypes.c_int, [_CTX]),
+    ("pp_last_error", ctypes.c_char_p, [_CTX]),
+    ("pp_version", ctypes.c_char_p, []),
+    ("pp_pairs_per_step", ctypes.c_double, [_I64]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building first if needed) the compiled library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not _build.up_to_date():
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, ctx=None):
+    if status != PP_OK:
+        msg = load().pp_last_error(ctx)
+        raise PPError(status, msg.decode() if msg else "")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _arg(x, n: int | None, writable: bool):
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        import torch
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise ValueError("device arrays must be contiguous float64")
+            if n is not None and tuple(x.shape) not in ((n, 3),):
+                raise ValueError(f"expected shape ({n}, 3), got {tuple(x.shape)}")
+            torch.cuda.current_stream(x.device).synchronize()
+            return x.data_ptr(), 1, x
+    a = x
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        if writable:
+            raise ValueError("output arrays must be C-contiguous float64")
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.shape != (n, 3):
+        raise ValueError(f"expected shape ({n}, 3), got {a.shape}")
+    return a.ctypes.data, 0, a
+
+
+def _same_kind(*ons):
+    ons = [o for o in ons if o is not None]
+    if len(set(ons)) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ons[0] if ons else 0
+
+
+# ---- the ABI, function by function --------------------------------------------
+
+def pp_version() -> str:
+    return load().pp_version().decode()
+
+
+def pp_pairs_per_step(n: int) -> float:
+    return load().pp_pairs_per_step(n)
+
+
+def pp_create(n: int, w: float, dt: float, softening: float):
+    ctx = _CTX()
+    _check(load().pp_create(int(n), float(w), float(dt), float(softening), ctypes.byref(ctx)))
+    return ctx
+
+
+def pp_set_option(ctx, key: int, value: int) -> None:
+    _check(load().pp_set_option(ctx, int(key), int(value)), ctx)
+
+
+def pp_get_n(ctx) -> int:
+    n = _I64()
+    _check(load().pp_get_n(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def pp_load_particles(ctx, pos, vel=None) -> None:
+    n = pp_get_n(ctx)
+    p, op, k1 = _arg(pos, n, False)
+    v, ov, k2 = _arg(vel, n, False)
+    on = _same_kind(op, ov if vel is not None else None)
+    _check(load().pp_load_particles(ctx, p, v, on), ctx)
+
+
+def pp_compute_fields(ctx, out=None):
+    """Field E [V/m], [N][3]; `out` may be a preallocated numpy array or CUDA tensor."""
+    n = pp_get_n(ctx)
+    if out is None:
+        out = np.empty((n, 3), dtype=np.float64)
+    p, on, keep = _arg(out, n, True)
+    _check(load().pp_compute_fields(ctx, p, on), ctx)
+    return out
+
+
+def pp_step(ctx, nsteps: int) -> None:
+    _check(load().pp_step(ctx, int(nsteps)), ctx)
+
+
+def pp_diagnostics(ctx, with_pe: bool = True) -> dict:
+    d = pp_diag()
+    _check(load().pp_diagnostics(ctx, ctypes.byref(d), 1 if with_pe else 0), ctx)
+    return d.as_dict()
+
+
+def pp_get_particles(ctx, pos=None, vel=None):
+    n = pp_get_n(ctx)
+    if pos is None and vel is None:
+        pos = np.empty((n, 3))
+        vel = np.empty((n, 3))
+    p, op, k1 = _arg(pos, n, True)
+    v, ov, k2 = _arg(vel, n, True)
+    on = _same_kind(op if pos is not None else None, ov if vel is not None else None)
+    _check(load().pp_get_particles(ctx, p, v, on), ctx)
+    return pos, vel
+
+
+def pp_get_state(ctx, pos=None, vel=None, acc=None):
+    n = pp_get_n(ctx)
+    if pos is None and vel is None and acc is None:
+        pos, vel, acc = (np.empty((n, 3)) for _ in range(3))
+    p, op, k1 = _arg(pos, n, True)
+    v, ov, k2 = _arg(vel, n, True)
+    a, oa, k3 = _arg(acc, n, True)
+    on = _same_kind(*(o for o, x in ((op, pos), (ov, vel), (oa, acc)) if x is not None))
+    step = _I64()
+    _check(load().pp_get_state(ctx, p, v, a, ctypes.byref(step), on), ctx)
+    return pos, vel, acc, step.value
+
+
+def pp_set_state(ctx, pos, vel, acc, step: int) -> None:
+    n = pp_get_n(ctx)
+    p, op, k1 = _arg(pos, n, False)
+    v, ov, k2 = _arg(vel, n, False)
+    a, oa, k3 = _arg(acc, n, False)
+    on = _same_kind(op, ov, oa)
+    _check(load().pp_set_state(ctx, p, v, a, int(step), on), ctx)
+
+
+def pp_destroy(ctx) -> None:
+    if ctx:
+        _check(load().pp_destroy(ctx))
+
+
+def pp_last_error(ctx=None) -> str:
+    m = load().pp_last_error(ctx)
+    return m.decode() if m else ""
+
+
+class Simulation:
+    """Owning wrapper: one context, destroyed with the object or on close()."""
+
+    def __init__(self, n: int, w: float, dt: float, softening: float = 0.0, acc: int | None = None):
+        self.ctx = pp_create(n, w, dt, softening)
+        self.n = n
+        if acc is not None:
+            pp_set_option(self.ctx, PP_OPT_ACC, acc)
+
+    def set_option(self, key, value):
+        pp_set_option(self.ctx, key, value)
+
+    def load(self, pos, vel=None):
+        pp_load_particles(self.ctx, pos, vel)
+
+    def fields(self, out=None):
+        return pp_compute_fields(self.ctx, out)
+
+    def step(self, nsteps: int = 1):
+        pp_step(self.ctx, nsteps)
+
+    def diagnostics(self, with_pe: bool = True) -> dict:
+        return pp_diagnostics(self.ctx, with_pe)
+
+    def particles(self):
+        return pp_get_particles(self.ctx)
+
+    def state(self):
+        return pp_get_state(self.ctx)
+
+    def set_state(self, pos, vel, acc, step):
+        pp_set_state(self.ctx, pos, vel, acc, step)
+
+    def close(self):
+        if self.ctx:
+            pp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

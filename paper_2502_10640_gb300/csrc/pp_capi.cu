@@ -1,0 +1,716 @@
+// pp_capi.cu -- the C ABI declared in include/pp.h: context lifetime, device
+// memory, launch planning (variant and j-split choice), CUDA-graph step
+// blocks, error words and status codes.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+#include "pp_internal.h"
+
+using namespace ppk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pp_status fail(pp_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+pp_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(PP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PP_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct pp_ctx {
+    int64_t n = 0;
+    int npad = 0;
+    double w = 1, dt = 0, eps = 0;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+
+    // FP64 state, SoA: r[3], v[3], a[3], each npad long, in one allocation.
+    double *state = nullptr;
+    double *r[3] = {}, *v[3] = {}, *a[3] = {};
+    void *stage[2] = {};           // float4 (or double4 for FP64 pair math) [npad]
+    size_t stage_bytes = 0;
+    double *aos = nullptr;         // [n][3] scratch for host transfers / outputs
+    double *phi = nullptr;         // [n]
+    double *partial = nullptr;     // split partials
+    size_t partial_bytes = 0;
+    unsigned *tickets = nullptr;
+    int tickets_cap = 0;
+    double *mom_partials = nullptr;
+    double *mom_out = nullptr;
+    int *err = nullptr;            // [0]: wait ran out, [1]: non-finite input
+    double *mom_host = nullptr;    // pinned
+
+    int parity = 0;
+    bool loaded = false;
+    int64_t step = 0;
+    double cx = 0, cy = 0, cz = 0, l0 = 1;
+
+    int acc = PP_ACC_FP64FOLD;
+    int split_override = 0;
+    int variant_override = -1;
+    int graph_block = 16;
+    uint64_t timeout_ns = 1000000000ull;
+    int skip_copy = 0;
+
+    // cached step graphs for (graph_block, start parity)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_steps = 0;
+};
+
+namespace {
+
+void drop_graphs(pp_ctx *c)
+{
+    for (auto &g : c->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    c->graph_steps = 0;
+}
+
+bool f64_pairs(const pp_ctx *c) { return c->acc == PP_ACC_FP64_FULL; }
+
+// Pick the variant for a kind and N (or the override).
+const Variant *pick_variant(const pp_ctx *c, int kind)
+{
+    int count = 0;
+    const Variant *vs = variants(&count);
+    if (kind == KIND_FORCE32 && c->variant_override >= 0 && c->variant_override < count &&
+        vs[c->variant_override].kind == KIND_FORCE32 && vs[c->variant_override].acc == c->acc)
+        return &vs[c->variant_override];
+    const char *want = nullptr;
+    if (kind == KIND_FORCE64) want = "f64.full.t128r2k128";
+    else if (kind == KIND_PHI32) want = c->n >= 32768 ? "phi32.fold64.t256r2k256" : "phi32.fold64.t128r1k128";
+    else if (c->acc == PP_ACC_KAHAN) want = c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128";
+    else if (c->n >= 32768) want = "f32.fold64.t256r4k256";
+    else if (c->n >= 4096) want = "f32.fold64.t128r2k128";
+    else want = "f32.fold64.t128r1k128";
+    for (int i = 0; i < count; ++i)
+        if (std::strcmp(vs[i].name, want) == 0) return &vs[i];
+    return &vs[0];
+}
+
+struct Plan {
+    const Variant *v;
+    int nib, nsplit, jchunk, grid, nipad;
+};
+
+// Choose S, the number of j-chunks per i-block, to fill the GPU: minimise
+// (waves of CTAs) x (tiles per CTA + fixed per-CTA overhead).
+Plan make_plan(pp_ctx *c, int kind)
+{
+    Plan pl{};
+    pl.v = pick_variant(c, kind);
+    const int BI = pl.v->T * pl.v->R;
+    pl.nib = (int)((c->n + BI - 1) / BI);
+    pl.nipad = pl.nib * BI;
+    const int tiles = c->npad / pl.v->tile;
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl.v->fn, pl.v->T, pl.v->smem);
+    if (occ < 1) occ = 1;
+    const int64_t slots = (int64_t)c->sms * occ;
+    int best_s = 1;
+    double best_cost = 1e300;
+    const int smax = std::min(tiles, 512);
+    for (int s = 1; s <= smax; ++s) {
+        const int chunk_tiles = (tiles + s - 1) / s;
+        const int s_eff = (tiles + chunk_tiles - 1) / chunk_tiles;
+        if (s_eff != s) continue;
+        const int64_t ctas = (int64_t)pl.nib * s;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double cost = (double)waves * (chunk_tiles + 1.5);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best_s = s;
+        }
+    }
+    if (c->split_override > 0) best_s = std::min(c->split_override, tiles);
+    const int chunk_tiles = (tiles + best_s - 1) / best_s;
+    pl.jchunk = chunk_tiles * pl.v->tile;
+    pl.nsplit = (tiles + chunk_tiles - 1) / chunk_tiles;
+    pl.grid = pl.nib * pl.nsplit;
+    return pl;
+}
+
+pp_status ensure_workspace(pp_ctx *c, const Plan &pl)
+{
+    const int ncomp = (pl.v->kind == KIND_PHI32) ? 1 : 3;
+    const size_t need = pl.nsplit > 1 ? (size_t)pl.nsplit * ncomp * pl.nipad * sizeof(double) : 0;
+    if (need > c->partial_bytes) {
+        if (c->partial) cudaFree(c->partial);
+        c->partial = nullptr;
+        c->partial_bytes = 0;
+        if (cudaMalloc(&c->partial, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PP_ERR_NOMEM, "cannot allocate the j-split workspace");
+        }
+        c->partial_bytes = need;
+        drop_graphs(c);
+    }
+    if (pl.nib > c->tickets_cap) {
+        if (c->tickets) cudaFree(c->tickets);
+        c->tickets = nullptr;
+        if (cudaMalloc(&c->tickets, pl.nib * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PP_ERR_NOMEM, "cannot allocate the ticket array");
+        }
+        PP_CUDA(cudaMemsetAsync(c->tickets, 0, pl.nib * sizeof(unsigned), c->stream));
+        c->tickets_cap = pl.nib;
+        drop_graphs(c);
+    }
+    return PP_OK;
+}
+
+ForceArgs base_args(const pp_ctx *c, const Plan &pl, int mode, const void *src, void *dst,
+                    double *out)
+{
+    ForceArgs a{};
+    a.src = src;
+    a.n = (int)c->n;
+    a.npad = c->npad;
+    a.nib = pl.nib;
+    a.nsplit = pl.nsplit;
+    a.jchunk = pl.jchunk;
+    a.mode = mode;
+    const double epsl = c->eps / c->l0;
+    a.eps2d = epsl * epsl;
+    a.eps2f = (float)a.eps2d;
+    a.partial = c->partial;
+    a.tickets = c->tickets;
+    a.nipad = pl.nipad;
+    for (int k = 0; k < 3; ++k) {
+        a.r[k] = c->r[k];
+        a.v[k] = c->v[k];
+        a.a[k] = c->a[k];
+    }
+    a.dst = dst;
+    a.out = out;
+    // a_i = k e^2 w / (m_e L0^2) * sum_j d'/|d'|^3   (Eq. F with Eq. E, staged units)
+    a.cscale = kCoulomb * kE * kE * c->w / (kMe * c->l0 * c->l0);
+    // E_i = (m_e / q_e) a_i, q_e = -e
+    a.escale = -kCoulomb * kE * c->w / (c->l0 * c->l0);
+    a.dt = c->dt;
+    a.half_dt = c->dt / 2.0;
+    a.half_dt2 = c->dt * c->dt / 2.0;
+    a.cx = c->cx;
+    a.cy = c->cy;
+    a.cz = c->cz;
+    a.inv_l0 = 1.0 / c->l0;
+    a.err = c->err;
+    a.timeout_ns = c->timeout_ns;
+    a.skip_copy = 0;
+    return a;
+}
+
+// Read and clear the device error word; maps it to a status.
+pp_status check_device_errors(pp_ctx *c, bool reset_state_on_timeout)
+{
+    int h[2] = {0, 0};
+    PP_CUDA(cudaMemcpyAsync(h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    if (h[0]) {
+        PP_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->stream));
+        if (c->tickets) PP_CUDA(cudaMemsetAsync(c->tickets, 0, c->tickets_cap * sizeof(unsigned), c->stream));
+        PP_CUDA(cudaStreamSynchronize(c->stream));
+        if (reset_state_on_timeout) c->loaded = false;
+        return fail(PP_ERR_TIMEOUT, "a device-side wait ran out of time; the particle state is "
+                                    "unspecified until particles are loaded or a state is set");
+    }
+    return PP_OK;
+}
+
+// One force pass over staged sources src.
+pp_status force_pass(pp_ctx *c, int mode, const void *src, void *dst, double *out)
+{
+    const int kind = (mode == MODE_PHI) ? KIND_PHI32 : (f64_pairs(c) ? KIND_FORCE64 : KIND_FORCE32);
+    const Plan pl = make_plan(c, kind);
+    pp_status st = ensure_workspace(c, pl);
+    if (st != PP_OK) return st;
+    ForceArgs a = base_args(c, pl, mode, src, dst, out);
+    a.skip_copy = c->skip_copy;
+    c->skip_copy = 0;
+    PP_CUDA(launch_variant(*pl.v, a, pl.grid, c->stream));
+    return PP_OK;
+}
+
+pp_status stage_current(pp_ctx *c, void *dst, bool f64)
+{
+    PP_CUDA(launch_stage(c->r[0], c->r[1], c->r[2], (int)c->n, c->npad, dst, f64, c->cx, c->cy,
+                         c->cz, 1.0 / c->l0, c->stream));
+    return PP_OK;
+}
+
+// Stage the pending positions drift(r_n, v_n, a_n) into stage[parity].
+pp_status restage_pending(pp_ctx *c)
+{
+    PP_CUDA(launch_stage_drift(c->r, c->v, c->a, (int)c->n, c->npad, c->stage[c->parity],
+                               f64_pairs(c), c->dt, c->dt * c->dt / 2.0, c->cx, c->cy, c->cz,
+                               1.0 / c->l0, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PP_OK;
+}
+
+// Copy [n][3] from the caller (host or device) into SoA dst; check finiteness.
+pp_status import_aos(pp_ctx *c, const double *src, int on_device, double *const dst[3])
+{
+    const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+    const double *dsrc = src;
+    if (!on_device) {
+        PP_CUDA(cudaMemcpyAsync(c->aos, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        dsrc = c->aos;
+    }
+    PP_CUDA(launch_aos_to_soa(dsrc, (int)c->n, dst[0], dst[1], dst[2], c->err + 1, c->stream));
+    return PP_OK;
+}
+
+pp_status export_aos(pp_ctx *c, double *const src[3], double *out, int on_device)
+{
+    const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+    double *target = on_device ? out : c->aos;
+    PP_CUDA(launch_soa_to_aos(src[0], src[1], src[2], (int)c->n, target, c->stream));
+    if (!on_device)
+        PP_CUDA(cudaMemcpyAsync(out, c->aos, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return PP_OK;
+}
+
+pp_status take_bad_input_flag(pp_ctx *c, bool *bad)
+{
+    int h = 0;
+    PP_CUDA(cudaMemcpyAsync(&h, c->err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
+    *bad = h != 0;
+    return PP_OK;
+}
+
+pp_status moments(pp_ctx *c, int pass, const double *x, double out[kMomSlots])
+{
+    PP_CUDA(launch_moments(pass, (int)c->n, pass == 2 ? x : c->r[0], c->r[1], c->r[2], c->v[0],
+                           c->v[1], c->v[2], c->cx, c->cy, c->cz, c->mom_partials, c->mom_out,
+                           c->stream));
+    PP_CUDA(cudaMemcpyAsync(c->mom_host, c->mom_out, kMomSlots * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, c->mom_host, kMomSlots * sizeof(double));
+    return PP_OK;
+}
+
+// Choose the staging frame: centre = centroid, L0 = power of two nearest the
+// RMS radius (so scaling by 1/L0 is exact).
+pp_status choose_frame(pp_ctx *c)
+{
+    double m[kMomSlots];
+    c->cx = c->cy = c->cz = 0.0;
+    pp_status st = moments(c, 0, nullptr, m);
+    if (st != PP_OK) return st;
+    const double n = (double)c->n;
+    const double cx = m[0] / n, cy = m[1] / n, cz = m[2] / n;
+    c->cx = cx;
+    c->cy = cy;
+    c->cz = cz;
+    st = moments(c, 1, nullptr, m);
+    if (st != PP_OK) return st;
+    const double rms = std::sqrt(m[0] / n);
+    double l0 = 1.0;
+    if (std::isfinite(rms) && rms > 0.0) {
+        int e = (int)std::lround(std::log2(rms));
+        e = std::max(-200, std::min(200, e));
+        l0 = std::ldexp(1.0, e);
+    }
+    c->l0 = l0;
+    return PP_OK;
+}
+
+bool graph_capturable(const pp_ctx *c) { return c->graph_block > 0 && c->stream != nullptr; }
+
+pp_status build_graphs(pp_ctx *c)
+{
+    drop_graphs(c);
+    const int kind = f64_pairs(c) ? KIND_FORCE64 : KIND_FORCE32;
+    const Plan pl = make_plan(c, kind);
+    pp_status st = ensure_workspace(c, pl);
+    if (st != PP_OK) return st;
+    for (int p0 = 0; p0 < 2; ++p0) {
+        cudaGraph_t g = nullptr;
+        PP_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int par = p0;
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < c->graph_block && le == cudaSuccess; ++k) {
+            ForceArgs a = base_args(c, pl, MODE_STEP, c->stage[par], c->stage[par ^ 1], nullptr);
+            le = launch_variant(*pl.v, a, pl.grid, c->stream);
+            par ^= 1;
+        }
+        cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+        if (le != cudaSuccess) return cuda_fail(le, "launch during graph capture");
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&c->graph[p0], g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    c->graph_steps = c->graph_block;
+    return PP_OK;
+}
+
+pp_status check_ctx(const pp_ctx *c)
+{
+    if (!c) return fail(PP_ERR_ARG, "null context");
+    return PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pp_version(void) { return "pp-gb300 0.1 (sm_103a)"; }
+
+const char *pp_last_error(const pp_ctx *) { return g_last_error.c_str(); }
+
+double pp_pairs_per_step(int64_t N) { return (double)N * (double)N; }
+
+pp_status pp_get_n(const pp_ctx *c, int64_t *n)
+{
+    if (!c || !n) return fail(PP_ERR_ARG, "null argument");
+    *n = c->n;
+    return PP_OK;
+}
+
+pp_status pp_destroy(pp_ctx *c)
+{
+    if (!c) return PP_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    cudaFree(c->state);
+    cudaFree(c->stage[0]);
+    cudaFree(c->stage[1]);
+    cudaFree(c->aos);
+    cudaFree(c->phi);
+    cudaFree(c->partial);
+    cudaFree(c->tickets);
+    cudaFree(c->mom_partials);
+    cudaFree(c->mom_out);
+    cudaFree(c->err);
+    if (c->mom_host) cudaFreeHost(c->mom_host);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+    return PP_OK;
+}
+
+pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **out)
+{
+    if (!out) return fail(PP_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (N < 1 || N > (int64_t(1) << 28)) return fail(PP_ERR_ARG, "N must be in [1, 2^28]");
+    if (!(std::isfinite(w) && w > 0)) return fail(PP_ERR_ARG, "w must be finite and > 0");
+    if (!(std::isfinite(dt) && dt > 0)) return fail(PP_ERR_ARG, "dt must be finite and > 0");
+    if (!(std::isfinite(softening) && softening >= 0))
+        return fail(PP_ERR_ARG, "softening must be finite and >= 0");
+    pp_ctx *c = new pp_ctx();
+    c->n = N;
+    c->npad = (int)round_up(N, kPad);
+    c->w = w;
+    c->dt = dt;
+    c->eps = softening;
+    auto bail = [&](pp_status s, const std::string &m) {
+        pp_destroy(c);
+        return fail(s, m);
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(PP_ERR_CUDA, "no CUDA device");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "cudaGetDeviceProperties failed");
+    c->sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "cudaStreamCreate failed");
+    c->stream = c->own_stream;
+    const size_t np = (size_t)c->npad;
+    c->stage_bytes = np * sizeof(double4);  // room for either staging type
+    bool okm = cudaMalloc(&c->state, 9 * np * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&c->stage[0], c->stage_bytes) == cudaSuccess &&
+               cudaMalloc(&c->stage[1], c->stage_bytes) == cudaSuccess &&
+               cudaMalloc(&c->aos, (size_t)N * 3 * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&c->phi, np * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&c->mom_partials, kMomBlocks * kMomSlots * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&c->mom_out, kMomSlots * sizeof(double)) == cudaSuccess &&
+               cudaMalloc(&c->err, 2 * sizeof(int)) == cudaSuccess &&
+               cudaMallocHost(&c->mom_host, kMomSlots * sizeof(double)) == cudaSuccess;
+    if (!okm) {
+        cudaGetLastError();
+        return bail(PP_ERR_NOMEM, "device allocation failed");
+    }
+    for (int k = 0; k < 3; ++k) {
+        c->r[k] = c->state + (0 + k) * np;
+        c->v[k] = c->state + (3 + k) * np;
+        c->a[k] = c->state + (6 + k) * np;
+    }
+    if (cudaMemsetAsync(c->state, 0, 9 * np * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "initial memset failed");
+    *out = c;
+    return PP_OK;
+}
+
+pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    switch (key) {
+    case PP_OPT_ACC:
+        if (value < PP_ACC_FP64FOLD || value > PP_ACC_FP64_FULL) return fail(PP_ERR_ARG, "bad acc mode");
+        if (value != c->acc) {
+            const bool was64 = f64_pairs(c);
+            c->acc = (int)value;
+            drop_graphs(c);
+            if (c->loaded && was64 != f64_pairs(c)) {
+                // the pending r_{n+1} is staged in the other precision: restage it
+                PP_CUDA(cudaSetDevice(c->device));
+                return restage_pending(c);
+            }
+        }
+        return PP_OK;
+    case PP_OPT_STREAM:
+        drop_graphs(c);
+        c->stream = value ? reinterpret_cast<cudaStream_t>(value) : c->own_stream;
+        return PP_OK;
+    case PP_OPT_SPLIT:
+        if (value < 0 || value > 4096) return fail(PP_ERR_ARG, "split must be in [0, 4096]");
+        c->split_override = (int)value;
+        drop_graphs(c);
+        return PP_OK;
+    case PP_OPT_GRAPH_BLOCK:
+        if (value < 0 || value > 4096) return fail(PP_ERR_ARG, "graph block must be in [0, 4096]");
+        c->graph_block = (int)value;
+        drop_graphs(c);
+        return PP_OK;
+    case PP_OPT_TIMEOUT_NS:
+        if (value < 1000 || value > 60000000000ll) return fail(PP_ERR_ARG, "timeout out of range");
+        c->timeout_ns = (uint64_t)value;
+        drop_graphs(c);
+        return PP_OK;
+    case PP_OPT_VARIANT: {
+        int count = 0;
+        variants(&count);
+        if (value < -1 || value >= count) return fail(PP_ERR_ARG, "no such variant");
+        c->variant_override = (int)value;
+        drop_graphs(c);
+        return PP_OK;
+    }
+    case PP_OPT_TEST_SKIP_COPY:
+        c->skip_copy = value ? 1 : 0;
+        return PP_OK;
+    default:
+        return fail(PP_ERR_ARG, "unknown option key");
+    }
+}
+
+pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int on_device)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!pos) return fail(PP_ERR_ARG, "pos is null");
+    PP_CUDA(cudaSetDevice(c->device));
+    drop_graphs(c);
+    c->loaded = false;
+    pp_status st = import_aos(c, pos, on_device, c->r);
+    if (st != PP_OK) return st;
+    if (vel) {
+        st = import_aos(c, vel, on_device, c->v);
+        if (st != PP_OK) return st;
+    } else {
+        for (int k = 0; k < 3; ++k)
+            PP_CUDA(cudaMemsetAsync(c->v[k], 0, c->npad * sizeof(double), c->stream));
+    }
+    bool bad = false;
+    st = take_bad_input_flag(c, &bad);
+    if (st != PP_OK) return st;
+    if (bad) return fail(PP_ERR_ARG, "non-finite position or velocity");
+    st = choose_frame(c);
+    if (st != PP_OK) return st;
+    // a_0 = F(r_0) (needed by the first Eq. G); the epilogue stages r_1.
+    c->parity = 0;
+    st = stage_current(c, c->stage[1], f64_pairs(c));
+    if (st != PP_OK) return st;
+    st = force_pass(c, MODE_INIT, c->stage[1], c->stage[0], nullptr);
+    if (st != PP_OK) return st;
+    st = check_device_errors(c, true);
+    if (st != PP_OK) return st;
+    c->loaded = true;
+    c->step = 0;
+    return PP_OK;
+}
+
+pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const double *acc,
+                       int64_t step, int on_device)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!pos || !vel || !acc) return fail(PP_ERR_ARG, "pos, vel and acc are required");
+    PP_CUDA(cudaSetDevice(c->device));
+    drop_graphs(c);
+    c->loaded = false;
+    pp_status st = import_aos(c, pos, on_device, c->r);
+    if (st == PP_OK) st = import_aos(c, vel, on_device, c->v);
+    if (st == PP_OK) st = import_aos(c, acc, on_device, c->a);
+    if (st != PP_OK) return st;
+    bool bad = false;
+    st = take_bad_input_flag(c, &bad);
+    if (st != PP_OK) return st;
+    if (bad) return fail(PP_ERR_ARG, "non-finite state");
+    st = choose_frame(c);
+    if (st != PP_OK) return st;
+    // stage r_{n+1} = Eq. G(r_n, v_n, a_n) exactly as the step epilogue would
+    c->parity = 0;
+    st = restage_pending(c);
+    if (st != PP_OK) return st;
+    c->loaded = true;
+    c->step = step;
+    return PP_OK;
+}
+
+pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t *step,
+                       int on_device)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
+    PP_CUDA(cudaSetDevice(c->device));
+    pp_status st;
+    if (pos && (st = export_aos(c, c->r, pos, on_device)) != PP_OK) return st;
+    if (vel && (st = export_aos(c, c->v, vel, on_device)) != PP_OK) return st;
+    if (acc && (st = export_aos(c, c->a, acc, on_device)) != PP_OK) return st;
+    if (step) *step = c->step;
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PP_OK;
+}
+
+pp_status pp_get_particles(pp_ctx *c, double *pos, double *vel, int on_device)
+{
+    return pp_get_state(c, pos, vel, nullptr, nullptr, on_device);
+}
+
+pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!E_out) return fail(PP_ERR_ARG, "E_out is null");
+    if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
+    PP_CUDA(cudaSetDevice(c->device));
+    // stage the current r_n into the idle buffer; the pending r_{n+1} stays put
+    void *scratch = c->stage[c->parity ^ 1];
+    pp_status st = stage_current(c, scratch, f64_pairs(c));
+    if (st != PP_OK) return st;
+    double *target = on_device ? E_out : c->aos;
+    st = force_pass(c, MODE_FIELDS, scratch, nullptr, target);
+    if (st != PP_OK) return st;
+    if (!on_device)
+        PP_CUDA(cudaMemcpyAsync(E_out, c->aos, (size_t)c->n * 3 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    return check_device_errors(c, false);
+}
+
+pp_status pp_step(pp_ctx *c, int64_t nsteps)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (nsteps < 0) return fail(PP_ERR_ARG, "nsteps must be >= 0");
+    if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
+    PP_CUDA(cudaSetDevice(c->device));
+    int64_t left = nsteps;
+    if (graph_capturable(c) && !c->skip_copy && left >= c->graph_block) {
+        if (c->graph_steps != c->graph_block || !c->graph[0]) {
+            pp_status st = build_graphs(c);
+            if (st != PP_OK) return st;
+        }
+        while (left >= c->graph_steps) {
+            PP_CUDA(cudaGraphLaunch(c->graph[c->parity], c->stream));
+            c->parity ^= (c->graph_steps & 1);
+            left -= c->graph_steps;
+        }
+    }
+    for (; left > 0; --left) {
+        pp_status st = force_pass(c, MODE_STEP, c->stage[c->parity], c->stage[c->parity ^ 1], nullptr);
+        if (st != PP_OK) return st;
+        c->parity ^= 1;
+    }
+    pp_status st = check_device_errors(c, true);
+    if (st != PP_OK) return st;
+    c->step += nsteps;
+    return PP_OK;
+}
+
+pp_status pp_diagnostics(pp_ctx *c, pp_diag *d, int with_pe)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!d) return fail(PP_ERR_ARG, "out is null");
+    if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
+    PP_CUDA(cudaSetDevice(c->device));
+    const double n = (double)c->n;
+    double m0[kMomSlots], m1[kMomSlots];
+    const double scx = c->cx, scy = c->cy, scz = c->cz;
+    c->cx = c->cy = c->cz = 0.0;
+    pp_status st = moments(c, 0, nullptr, m0);
+    if (st != PP_OK) return st;
+    const double cx = m0[0] / n, cy = m0[1] / n, cz = m0[2] / n;
+    c->cx = cx;
+    c->cy = cy;
+    c->cz = cz;
+    st = moments(c, 1, nullptr, m1);
+    c->cx = scx;
+    c->cy = scy;
+    c->cz = scz;
+    if (st != PP_OK) return st;
+    const double mw = kMe * c->w;
+    d->t = (double)c->step * c->dt;
+    d->step = c->step;
+    d->rms_radius = std::sqrt(m1[0] / n);
+    d->ke = 0.5 * mw * m1[1];
+    d->px = mw * m1[2];
+    d->py = mw * m1[3];
+    d->pz = mw * m1[4];
+    const double x2 = m1[5] / n, vx2 = m1[6] / n, xvx = m1[7] / n;
+    const double e2 = x2 * vx2 - xvx * xvx;
+    d->emit_x = std::sqrt(e2 > 0 ? e2 : 0.0);
+    d->x_rms = std::sqrt(x2);
+    d->x_max = m1[10];
+    d->vx_rms = std::sqrt(vx2);
+    d->vx_max = m1[11];
+    d->cx = cx;
+    d->cy = cy;
+    d->cz = cz;
+    d->pe = NAN;
+    if (with_pe) {
+        // phi'_i = sum_{j != i} 1/sqrt(|d'|^2 + eps'^2); PE = 1/2 k e^2 w^2 / L0 * sum_i phi'_i
+        // the potential pass always uses FP32 sources, staged into the idle buffer
+        void *scratch = c->stage[c->parity ^ 1];
+        st = stage_current(c, scratch, false);
+        if (st == PP_OK) st = force_pass(c, MODE_PHI, scratch, nullptr, c->phi);
+        if (st != PP_OK) return st;
+        st = check_device_errors(c, false);
+        if (st != PP_OK) return st;
+        double mp[kMomSlots];
+        st = moments(c, 2, c->phi, mp);
+        if (st != PP_OK) return st;
+        d->pe = 0.5 * kCoulomb * kE * kE * c->w * c->w / c->l0 * mp[0];
+    }
+    return PP_OK;
+}
+
+}  // extern "C"

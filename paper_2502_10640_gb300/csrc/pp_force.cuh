@@ -1,0 +1,601 @@
+// pp_force.cuh -- the O(N^2) direct Coulomb sum (arXiv 2502.10640, Eq. B/E)
+// with the Velocity-Verlet push (Eq. G/H) fused into its epilogue.
+//
+// Work decomposition.  A CTA owns BI = T*R target particles i (R per thread,
+// strided by T so loads coalesce) and one j-chunk of the staged source array.
+// With S > 1 chunks per i-block, each CTA writes FP64 partial sums, and the
+// CTA that finishes an i-block last (an atomic ticket decides who) adds the S
+// partials in the fixed order s = 0..S-1 and runs the epilogue.  The ticket
+// picks only *who* sums, never the order, so results are bitwise reproducible.
+//
+// Data movement.  Staged sources are float4 (x', y', z', q') in units of a
+// power-of-two length L0 about a fixed centre.  One thread streams TILE-sized
+// j-tiles through a STAGES-deep shared-memory ring with 1D bulk copies (TMA)
+// tracked by mbarriers; every warp releases a stage through an "empty"
+// mbarrier, after which the producer refills it.  All waits are bounded.
+//
+// Pair math (per pair, FP32): d = r_i - r_j; s = d.d + eps'^2;
+// inv = rsqrt(s) on the SFU; acc += inv^3 * d.  Equal weights factor out of
+// the sum (Sec. 2.1), so no per-pair weight multiply is needed.
+// Per TILE the FP32 partials are folded into FP64 (or into a compensated FP32
+// hi/lo pair); a non-finite tile partial (a pair with s == 0: the self pair
+// when eps = 0, or coincident particles) is recomputed for that particle with
+// the zero-distance pairs skipped, which is the reading of Eq. B used here.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pp_device.cuh"
+
+namespace ppk {
+
+enum Mode : int {
+    MODE_STEP = 0,    // a_{n+1} from staged r_{n+1}; epilogue: Eq. G recompute, Eq. H, stage r_{n+2}
+    MODE_FIELDS = 1,  // E = escale * sum, written [N][3]; state untouched
+    MODE_INIT = 2,    // a_0 from staged r_0; epilogue: store a_0, stage r_1 (Eq. G)
+    MODE_PHI = 3      // phi'_i = sum_{j != i} 1/sqrt(s); written [N]
+};
+
+enum Acc : int { ACC_FP64FOLD = 0, ACC_KAHAN = 1, ACC_FP64FULL = 2 };
+
+struct ForceArgs {
+    const void *src;        // staged sources: float4[npad] (or double4[npad] for FP64 pair math)
+    int n;                  // real particles
+    int npad;               // staged length (multiple of the tile)
+    int nib;                // i-blocks
+    int nsplit;             // j-chunks per i-block (S)
+    int jchunk;             // sources per chunk (multiple of the tile)
+    int mode;
+    float eps2f;            // (eps / L0)^2
+    double eps2d;
+    double *partial;        // [S][3][nipad] FP64 partial sums (S > 1)
+    unsigned *tickets;      // [nib] arrival counters, zero between launches
+    int nipad;              // nib * BI
+    double *r[3];           // state, SoA, [n] each
+    double *v[3];
+    double *a[3];
+    void *dst;              // staging written by the epilogue (float4 or double4)
+    double *out;            // fields [n][3] (MODE_FIELDS) or phi [n] (MODE_PHI)
+    double cscale;          // a = cscale * sum
+    double escale;          // E = escale * sum
+    double dt, half_dt, half_dt2;
+    double cx, cy, cz, inv_l0;
+    int *err;               // device error word (bit 0: a wait ran out)
+    unsigned long long timeout_ns;
+    int skip_copy;          // test hook: CTA 0 withholds its last tile copy
+};
+
+// ---- FP64 push arithmetic, written so that no multiply-add is fused: the
+// drift of Eq. G is evaluated as (r + v dt) + a (dt^2/2) and the kick of
+// Eq. H as v + (a_old + a_new) (dt/2), each operation rounded once.
+__device__ __forceinline__ double drift(double r, double v, double a, double dt, double half_dt2)
+{
+    return __dadd_rn(__dadd_rn(r, __dmul_rn(v, dt)), __dmul_rn(a, half_dt2));
+}
+
+__device__ __forceinline__ double kick(double v, double a_old, double a_new, double half_dt)
+{
+    return __dadd_rn(v, __dmul_rn(__dadd_rn(a_old, a_new), half_dt));
+}
+
+template <class E>
+__device__ __forceinline__ E stage_value(double x, double y, double z, const ForceArgs &p);
+
+template <>
+__device__ __forceinline__ float4 stage_value<float4>(double x, double y, double z,
+                                                      const ForceArgs &p)
+{
+    return make_float4(__double2float_rn(__dmul_rn(__dsub_rn(x, p.cx), p.inv_l0)),
+                       __double2float_rn(__dmul_rn(__dsub_rn(y, p.cy), p.inv_l0)),
+                       __double2float_rn(__dmul_rn(__dsub_rn(z, p.cz), p.inv_l0)), 1.0f);
+}
+
+template <>
+__device__ __forceinline__ double4 stage_value<double4>(double x, double y, double z,
+                                                        const ForceArgs &p)
+{
+    return make_double4(__dmul_rn(__dsub_rn(x, p.cx), p.inv_l0),
+                        __dmul_rn(__dsub_rn(y, p.cy), p.inv_l0),
+                        __dmul_rn(__dsub_rn(z, p.cz), p.inv_l0), 1.0);
+}
+
+// Epilogue for particle i given its full FP64 sum (staged units).
+template <class E>
+__device__ __forceinline__ void finish_particle(const ForceArgs &p, int i, double sx, double sy,
+                                                double sz)
+{
+    if (i >= p.n) return;
+    if (p.mode == MODE_FIELDS) {
+        p.out[3 * (size_t)i + 0] = p.escale * sx;
+        p.out[3 * (size_t)i + 1] = p.escale * sy;
+        p.out[3 * (size_t)i + 2] = p.escale * sz;
+        return;
+    }
+    if (p.mode == MODE_PHI) {
+        p.out[i] = sx;
+        return;
+    }
+    const double an[3] = {p.cscale * sx, p.cscale * sy, p.cscale * sz};
+    double rn[3];
+    if (p.mode == MODE_STEP) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double r0 = p.r[c][i], v0 = p.v[c][i], a0 = p.a[c][i];
+            const double r1 = drift(r0, v0, a0, p.dt, p.half_dt2);   // Eq. G (as staged)
+            const double v1 = kick(v0, a0, an[c], p.half_dt);         // Eq. H
+            p.r[c][i] = r1;
+            p.v[c][i] = v1;
+            p.a[c][i] = an[c];
+            rn[c] = drift(r1, v1, an[c], p.dt, p.half_dt2);           // next Eq. G, staged only
+        }
+    } else {  // MODE_INIT
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            p.a[c][i] = an[c];
+            rn[c] = drift(p.r[c][i], p.v[c][i], an[c], p.dt, p.half_dt2);
+        }
+    }
+    static_cast<E *>(p.dst)[i] = stage_value<E>(rn[0], rn[1], rn[2], p);
+}
+
+// Shared-memory ring + barriers of one CTA.
+template <class E, int TILE, int STAGES>
+struct Ring {
+    E *buf;
+    uint64_t *full;
+    uint64_t *empty;
+};
+
+// Warp-uniform bounded wait: lane 0 waits (bounded), the verdict is shared
+// with the warp, then every lane observes the completed phase itself (which
+// gives each thread acquire ordering on the bulk-copied data).  All lanes
+// return the same value, so no lane can leave the warp behind at a later
+// warp-synchronous point.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity, limit_ns) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    const int mine = mbar_wait_bounded(bar, parity, limit_ns) ? 1 : 0;
+    return __all_sync(0xffffffffu, mine) != 0;
+}
+
+// Stream the CTA's j-tiles through the ring and call body(tile, j_first) for
+// each.  Returns false if a wait ran out; the value is uniform within each
+// warp.  On false the caller must run ring_drain before the CTA exits.
+template <class E, int T, int TILE, int STAGES, class Body>
+__device__ __forceinline__ bool run_tiles(const ForceArgs &p, const Ring<E, TILE, STAGES> &rg,
+                                          int j0, int ntiles, int &issued, int &seen, Body &&body)
+{
+    const int tid = threadIdx.x;
+    const E *src = static_cast<const E *>(p.src);
+    constexpr uint32_t kBytes = TILE * sizeof(E);
+    auto issue = [&](int t) {
+        const int s = t % STAGES;
+        mbar_arrive_expect_tx(&rg.full[s], kBytes);
+        const bool withhold = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
+        if (!withhold) bulk_g2s(rg.buf + s * TILE, src + j0 + (size_t)t * TILE, kBytes, &rg.full[s]);
+    };
+    if (tid == 0) {
+        for (int t = 0; t < STAGES && t < ntiles; ++t) issue(t);
+        issued = ntiles < STAGES ? ntiles : STAGES;
+    }
+    for (int t = 0; t < ntiles; ++t) {
+        const int s = t % STAGES;
+        const uint32_t ph = (t / STAGES) & 1;
+        if (!warp_wait(&rg.full[s], ph, p.timeout_ns)) return false;
+        if (tid == 0) seen = t + 1;
+        body(rg.buf + s * TILE, j0 + t * TILE);
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&rg.empty[s]);
+        if (tid < 32 && t + STAGES < ntiles) {   // warp 0: lane 0 refills the stage
+            int ok = 1;
+            if (tid == 0) {
+                ok = mbar_wait_bounded(&rg.empty[s], ph, p.timeout_ns) ? 1 : 0;
+                if (ok) {
+                    issue(t + STAGES);
+                    issued = t + STAGES + 1;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+        }
+    }
+    return true;
+}
+
+// After a failed wait: thread 0 waits (bounded) for copies it issued that
+// have not been observed complete, so no bulk copy still targets shared
+// memory when the CTA exits.
+template <class E, int TILE, int STAGES>
+__device__ __forceinline__ void ring_drain(const ForceArgs &p, const Ring<E, TILE, STAGES> &rg,
+                                           int issued, int seen, int ntiles)
+{
+    if (threadIdx.x != 0) return;
+    for (int t = seen; t < issued; ++t) {
+        const bool withheld = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
+        if (withheld) continue;
+        mbar_wait_bounded(&rg.full[t % STAGES], (t / STAGES) & 1, p.timeout_ns);
+    }
+}
+
+// ---- pair loops ----------------------------------------------------------
+
+// Fast loop: TILE sources against R targets, no checks.
+template <int R, int TILE>
+__device__ __forceinline__ void tile_fast(const float4 *__restrict__ tile, const float (&xi)[R],
+                                          const float (&yi)[R], const float (&zi)[R], float eps2,
+                                          float (&fx)[R], float (&fy)[R], float (&fz)[R])
+{
+#pragma unroll 4
+    for (int j = 0; j < TILE; ++j) {
+        const float4 q = tile[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float dx = xi[r] - q.x;
+            const float dy = yi[r] - q.y;
+            const float dz = zi[r] - q.z;
+            const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+            const float inv = rsqrt_sfu(s);
+            const float inv3 = inv * inv * inv;
+            fx[r] = fmaf(inv3, dx, fx[r]);
+            fy[r] = fmaf(inv3, dy, fy[r]);
+            fz[r] = fmaf(inv3, dz, fz[r]);
+        }
+    }
+}
+
+// Safe loop for one target: pairs with s == 0 add nothing.  Same operations
+// in the same order as tile_fast for every other pair.
+template <int TILE>
+__device__ __noinline__ float3 tile_safe1(const float4 *__restrict__ tile, float x, float y,
+                                          float z, float eps2)
+{
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int j = 0; j < TILE; ++j) {
+        const float4 q = tile[j];
+        const float dx = x - q.x;
+        const float dy = y - q.y;
+        const float dz = z - q.z;
+        const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        if (s > 0.f) {
+            const float inv = rsqrt_sfu(s);
+            const float inv3 = inv * inv * inv;
+            ax = fmaf(inv3, dx, ax);
+            ay = fmaf(inv3, dy, ay);
+            az = fmaf(inv3, dz, az);
+        }
+    }
+    return make_float3(ax, ay, az);
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Split-path epilogue shared by all kernels: write partials, take a ticket,
+// and let the last CTA of the i-block sum the S partials in order s = 0..S-1.
+// Returns true on the CTA that must finish the i-block.
+template <int T, int R>
+__device__ __forceinline__ bool split_publish(const ForceArgs &p, int ib, int split,
+                                              const double (&sx)[R], const double (&sy)[R],
+                                              const double (&sz)[R], int ncomp, int *s_flag)
+{
+    const int tid = threadIdx.x;
+    const size_t stride = (size_t)p.nipad;
+    double *base = p.partial + (size_t)split * ncomp * stride;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = ib * T * R + r * T + tid;
+        base[i] = sx[r];
+        if (ncomp == 3) {
+            base[stride + i] = sy[r];
+            base[2 * stride + i] = sz[r];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&p.tickets[ib], 1u);
+        *s_flag = (prev == (unsigned)(p.nsplit - 1));
+    }
+    __syncthreads();
+    if (!*s_flag) return false;
+    __threadfence();
+    return true;
+}
+
+template <int T, int R>
+__device__ __forceinline__ void split_gather(const ForceArgs &p, int ib, double (&sx)[R],
+                                             double (&sy)[R], double (&sz)[R], int ncomp)
+{
+    const int tid = threadIdx.x;
+    const size_t stride = (size_t)p.nipad;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = ib * T * R + r * T + tid;
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int s = 0; s < p.nsplit; ++s) {
+            const double *base = p.partial + (size_t)s * ncomp * stride;
+            ax += ld_cg(base + i);
+            if (ncomp == 3) {
+                ay += ld_cg(base + stride + i);
+                az += ld_cg(base + 2 * stride + i);
+            }
+        }
+        sx[r] = ax;
+        sy[r] = ay;
+        sz[r] = az;
+    }
+    if (tid == 0) p.tickets[ib] = 0u;
+}
+
+// ---- FP32 pair math, FP64 or compensated fold ------------------------------
+template <int T, int R, int TILE, int STAGES, int ACC, int MINB>
+__global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
+{
+    constexpr int BI = T * R;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ int s_abort, s_flag;
+
+    const int tid = threadIdx.x;
+    const int ib = blockIdx.x % p.nib;
+    const int split = blockIdx.x / p.nib;
+    const int i0 = ib * BI;
+    const int j0 = split * p.jchunk;
+    const int j1 = min(j0 + p.jchunk, p.npad);
+    const int ntiles = (j1 - j0) / TILE;
+
+    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), bar_full, bar_empty};
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], T / 32);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const float4 *src = static_cast<const float4 *>(p.src);
+    float xi[R], yi[R], zi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        // targets past n sit far away from every source and from the padding
+        const float4 q = (i < p.n) ? src[i] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+        xi[r] = q.x;
+        yi[r] = q.y;
+        zi[r] = q.z;
+    }
+
+    double dx64[R], dy64[R], dz64[R];  // FP64 fold (ACC_FP64FOLD)
+    float hx[R], hy[R], hz[R], lx[R], ly[R], lz[R];  // compensated fold (ACC_KAHAN)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        dx64[r] = dy64[r] = dz64[r] = 0.0;
+        hx[r] = hy[r] = hz[r] = lx[r] = ly[r] = lz[r] = 0.f;
+    }
+    const float eps2 = p.eps2f;
+
+    int issued = 0, seen = 0;
+    const bool ok = run_tiles<float4, T, TILE, STAGES>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, int) {
+            float fx[R], fy[R], fz[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) fx[r] = fy[r] = fz[r] = 0.f;
+            tile_fast<R, TILE>(tile, xi, yi, zi, eps2, fx, fy, fz);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!isfinite(fx[r] + fy[r] + fz[r])) {
+                    const float3 f = tile_safe1<TILE>(tile, xi[r], yi[r], zi[r], eps2);
+                    fx[r] = f.x;
+                    fy[r] = f.y;
+                    fz[r] = f.z;
+                }
+                if (ACC == ACC_KAHAN) {
+                    float s, e;
+                    two_sum(hx[r], fx[r], s, e); hx[r] = s; lx[r] = __fadd_rn(lx[r], e);
+                    two_sum(hy[r], fy[r], s, e); hy[r] = s; ly[r] = __fadd_rn(ly[r], e);
+                    two_sum(hz[r], fz[r], s, e); hz[r] = s; lz[r] = __fadd_rn(lz[r], e);
+                } else {
+                    dx64[r] += (double)fx[r];
+                    dy64[r] += (double)fy[r];
+                    dz64[r] += (double)fz[r];
+                }
+            }
+        });
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(p.err, 1);
+    }
+    __syncthreads();
+    if (s_abort) {
+        ring_drain<float4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        return;
+    }
+    if (ACC == ACC_KAHAN) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            dx64[r] = (double)hx[r] + (double)lx[r];
+            dy64[r] = (double)hy[r] + (double)ly[r];
+            dz64[r] = (double)hz[r] + (double)lz[r];
+        }
+    }
+    if (p.nsplit > 1) {
+        if (!split_publish<T, R>(p, ib, split, dx64, dy64, dz64, 3, &s_flag)) return;
+        split_gather<T, R>(p, ib, dx64, dy64, dz64, 3);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        finish_particle<float4>(p, i0 + r * T + tid, dx64[r], dy64[r], dz64[r]);
+}
+
+// ---- potential: phi'_i = sum_{j != i, s > 0} 1/sqrt(s), FP32 pairs, FP64 fold ----
+template <int T, int R, int TILE, int STAGES>
+__global__ void __launch_bounds__(T) phi_f32_kernel(const ForceArgs p)
+{
+    constexpr int BI = T * R;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ int s_abort, s_flag;
+
+    const int tid = threadIdx.x;
+    const int ib = blockIdx.x % p.nib;
+    const int split = blockIdx.x / p.nib;
+    const int i0 = ib * BI;
+    const int j0 = split * p.jchunk;
+    const int j1 = min(j0 + p.jchunk, p.npad);
+    const int ntiles = (j1 - j0) / TILE;
+
+    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), bar_full, bar_empty};
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], T / 32);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const float4 *src = static_cast<const float4 *>(p.src);
+    float xi[R], yi[R], zi[R];
+    int gi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        gi[r] = i;
+        const float4 q = (i < p.n) ? src[i] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+        xi[r] = q.x;
+        yi[r] = q.y;
+        zi[r] = q.z;
+    }
+    double acc[R], dummy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = dummy[r] = 0.0;
+    const float eps2 = p.eps2f;
+    int issued = 0, seen = 0;
+    const bool ok = run_tiles<float4, T, TILE, STAGES>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, int jfirst) {
+            float f[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) f[r] = 0.f;
+            for (int j = 0; j < TILE; ++j) {
+                const float4 q = tile[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dx = xi[r] - q.x;
+                    const float dy = yi[r] - q.y;
+                    const float dz = zi[r] - q.z;
+                    const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+                    // padding sources carry q.w = 0
+                    const float term = (s > 0.f && jfirst + j != gi[r]) ? q.w * rsqrt_sfu(s) : 0.f;
+                    f[r] += term;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += (double)f[r];
+        });
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(p.err, 1);
+    }
+    __syncthreads();
+    if (s_abort) {
+        ring_drain<float4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        return;
+    }
+    if (p.nsplit > 1) {
+        if (!split_publish<T, R>(p, ib, split, acc, dummy, dummy, 1, &s_flag)) return;
+        split_gather<T, R>(p, ib, acc, dummy, dummy, 1);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) finish_particle<float4>(p, i0 + r * T + tid, acc[r], 0.0, 0.0);
+}
+
+// ---- FP64 pair math and accumulation (comparison path) ---------------------
+template <int T, int R, int TILE, int STAGES>
+__global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
+{
+    constexpr int BI = T * R;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ int s_abort, s_flag;
+
+    const int tid = threadIdx.x;
+    const int ib = blockIdx.x % p.nib;
+    const int split = blockIdx.x / p.nib;
+    const int i0 = ib * BI;
+    const int j0 = split * p.jchunk;
+    const int j1 = min(j0 + p.jchunk, p.npad);
+    const int ntiles = (j1 - j0) / TILE;
+
+    Ring<double4, TILE, STAGES> rg{reinterpret_cast<double4 *>(smem_raw), bar_full, bar_empty};
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], T / 32);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const double4 *src = static_cast<const double4 *>(p.src);
+    double xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        const double4 q = (i < p.n) ? src[i] : make_double4(-1e18, -1e18, -1e18, 0.0);
+        xi[r] = q.x;
+        yi[r] = q.y;
+        zi[r] = q.z;
+        ax[r] = ay[r] = az[r] = 0.0;
+    }
+    const double eps2 = p.eps2d;
+    int issued = 0, seen = 0;
+    const bool ok = run_tiles<double4, T, TILE, STAGES>(
+        p, rg, j0, ntiles, issued, seen, [&](const double4 *tile, int) {
+            for (int j = 0; j < TILE; ++j) {
+                const double4 q = tile[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const double dx = xi[r] - q.x;
+                    const double dy = yi[r] - q.y;
+                    const double dz = zi[r] - q.z;
+                    const double s = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+                    if (s > 0.0) {
+                        const double inv = rsqrt(s);
+                        const double inv3 = inv * inv * inv;
+                        ax[r] = fma(inv3, dx, ax[r]);
+                        ay[r] = fma(inv3, dy, ay[r]);
+                        az[r] = fma(inv3, dz, az[r]);
+                    }
+                }
+            }
+        });
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(p.err, 1);
+    }
+    __syncthreads();
+    if (s_abort) {
+        ring_drain<double4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        return;
+    }
+    if (p.nsplit > 1) {
+        if (!split_publish<T, R>(p, ib, split, ax, ay, az, 3, &s_flag)) return;
+        split_gather<T, R>(p, ib, ax, ay, az, 3);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) finish_particle<double4>(p, i0 + r * T + tid, ax[r], ay[r], az[r]);
+}
+
+}  // namespace ppk

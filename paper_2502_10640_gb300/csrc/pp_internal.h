@@ -1,0 +1,70 @@
+// pp_internal.h -- host-side interface between the C ABI layer and the
+// kernel translation unit.  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pp_force.cuh"
+
+namespace ppk {
+
+// CODATA 2018 (SI).  The paper prints no constants.
+constexpr double kE = 1.602176634e-19;      // elementary charge, C (exact)
+constexpr double kMe = 9.1093837015e-31;    // electron mass, kg
+constexpr double kEps0 = 8.8541878128e-12;  // vacuum permittivity, F/m
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);  // 1/(4 pi eps0), Eq. A
+
+// Staged arrays are padded to a multiple of this many entries.
+constexpr int kPad = 1024;
+
+enum Kind : int { KIND_FORCE32 = 0, KIND_PHI32 = 1, KIND_FORCE64 = 2 };
+
+struct Variant {
+    const char *name;
+    int kind;
+    int acc;      // Acc
+    int T, R, tile, stages;
+    const void *fn;
+    size_t smem;  // dynamic shared memory bytes
+};
+
+// Table of compiled force-kernel variants.
+const Variant *variants(int *count);
+
+// Launch one variant with the given arguments on `stream`.
+cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaStream_t stream);
+
+// Deterministic O(N) kernels.
+// AoS [n][3] -> three SoA arrays; sets *bad to 1 if any input is not finite.
+cudaError_t launch_aos_to_soa(const double *in, int n, double *x, double *y, double *z, int *bad,
+                              cudaStream_t s);
+cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z, int n,
+                              double *out, cudaStream_t s);
+// Stage FP64 positions into float4 (or double4) sources; entries n..npad-1
+// become padding (far away, weight 0).
+cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
+                         void *dst, bool f64, double cx, double cy, double cz, double inv_l0,
+                         cudaStream_t s);
+
+// Stage the next positions of Eq. G, drift(r, v, a), exactly as the step
+// epilogue stages them (used after a state is restored).
+cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
+                               int npad, void *dst, bool f64, double dt, double half_dt2,
+                               double cx, double cy, double cz, double inv_l0, cudaStream_t s);
+
+// Moments over n particles in a fixed reduction order.
+//  pass 0: sums of x, y, z                                     -> out[0..2]
+//  pass 1: sum |r-c|^2, sum |v|^2, sum vx, vy, vz, sum x^2,
+//          sum vx^2, sum x vx (out[0..7]); max x, max vx (out[10], out[11])
+//  pass 2: sum of the values in x (one array)                  -> out[0]
+constexpr int kMomSlots = 12;
+constexpr int kMomBlocks = 240;
+cudaError_t launch_moments(int pass, int n, const double *x, const double *y, const double *z,
+                           const double *vx, const double *vy, const double *vz, double cx,
+                           double cy, double cz, double *block_partials, double *out,
+                           cudaStream_t s);
+
+}  // namespace ppk

@@ -1,0 +1,275 @@
+// pp_kernels.cu -- compiled force-kernel variants and the O(N) helper kernels
+// (layout conversion, staging, deterministic moment reductions).
+#include <cfloat>
+#include <cmath>
+
+#include "pp_internal.h"
+
+namespace ppk {
+
+namespace {
+
+template <int T, int R, int TILE, int STAGES, int ACC, int MINB>
+Variant make_f32(const char *name)
+{
+    return Variant{name, KIND_FORCE32, ACC, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(&force_f32_kernel<T, R, TILE, STAGES, ACC, MINB>),
+                   (size_t)STAGES * TILE * sizeof(float4)};
+}
+
+template <int T, int R, int TILE, int STAGES>
+Variant make_phi(const char *name)
+{
+    return Variant{name, KIND_PHI32, ACC_FP64FOLD, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(&phi_f32_kernel<T, R, TILE, STAGES>),
+                   (size_t)STAGES * TILE * sizeof(float4)};
+}
+
+template <int T, int R, int TILE, int STAGES>
+Variant make_f64(const char *name)
+{
+    return Variant{name, KIND_FORCE64, ACC_FP64FULL, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(&force_f64_kernel<T, R, TILE, STAGES>),
+                   (size_t)STAGES * TILE * sizeof(double4)};
+}
+
+const Variant kVariants[] = {
+    make_f32<256, 4, 256, 4, ACC_FP64FOLD, 2>("f32.fold64.t256r4k256"),
+    make_f32<256, 8, 256, 4, ACC_FP64FOLD, 1>("f32.fold64.t256r8k256"),
+    make_f32<128, 2, 128, 4, ACC_FP64FOLD, 4>("f32.fold64.t128r2k128"),
+    make_f32<128, 1, 128, 4, ACC_FP64FOLD, 4>("f32.fold64.t128r1k128"),
+    make_f32<256, 4, 256, 4, ACC_KAHAN, 2>("f32.kahan.t256r4k256"),
+    make_f32<128, 2, 128, 4, ACC_KAHAN, 4>("f32.kahan.t128r2k128"),
+    make_phi<256, 2, 256, 4>("phi32.fold64.t256r2k256"),
+    make_phi<128, 1, 128, 4>("phi32.fold64.t128r1k128"),
+    make_f64<128, 2, 128, 3>("f64.full.t128r2k128"),
+};
+
+}  // namespace
+
+const Variant *variants(int *count)
+{
+    *count = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+    return kVariants;
+}
+
+cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaStream_t stream)
+{
+    static bool configured[sizeof(kVariants) / sizeof(kVariants[0])] = {};
+    const int idx = (int)(&v - kVariants);
+    if (idx >= 0 && idx < (int)(sizeof(kVariants) / sizeof(kVariants[0])) && !configured[idx]) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)v.smem);
+        if (e != cudaSuccess) return e;
+        configured[idx] = true;
+    }
+    ForceArgs copy = a;
+    void *args[] = {&copy};
+    return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.T), args, v.smem, stream);
+}
+
+// ---- O(N) kernels ----------------------------------------------------------
+
+namespace {
+
+__global__ void aos_to_soa_kernel(const double *__restrict__ in, int n, double *x, double *y,
+                                  double *z, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double a = in[3 * (size_t)i], b = in[3 * (size_t)i + 1], c = in[3 * (size_t)i + 2];
+        if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(bad, 1);
+        x[i] = a;
+        y[i] = b;
+        z[i] = c;
+    }
+}
+
+__global__ void soa_to_aos_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                                  const double *__restrict__ z, int n, double *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[3 * (size_t)i] = x[i];
+        out[3 * (size_t)i + 1] = y[i];
+        out[3 * (size_t)i + 2] = z[i];
+    }
+}
+
+__global__ void stage_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                             const double *__restrict__ z, int n, int npad, void *dst, int f64,
+                             double cx, double cy, double cz, double inv_l0)
+{
+    ForceArgs p{};
+    p.cx = cx;
+    p.cy = cy;
+    p.cz = cz;
+    p.inv_l0 = inv_l0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+        if (f64) {
+            double4 *d = static_cast<double4 *>(dst);
+            d[i] = (i < n) ? stage_value<double4>(x[i], y[i], z[i], p)
+                           : make_double4(1e18, 1e18, 1e18, 0.0);
+        } else {
+            float4 *d = static_cast<float4 *>(dst);
+            d[i] = (i < n) ? stage_value<float4>(x[i], y[i], z[i], p)
+                           : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        }
+    }
+}
+
+__global__ void stage_drift_kernel(const double *__restrict__ rx, const double *__restrict__ ry,
+                                   const double *__restrict__ rz, const double *__restrict__ vx,
+                                   const double *__restrict__ vy, const double *__restrict__ vz,
+                                   const double *__restrict__ ax, const double *__restrict__ ay,
+                                   const double *__restrict__ az, int n, int npad, void *dst,
+                                   int f64, double dt, double half_dt2, double cx, double cy,
+                                   double cz, double inv_l0)
+{
+    ForceArgs p{};
+    p.cx = cx;
+    p.cy = cy;
+    p.cz = cz;
+    p.inv_l0 = inv_l0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double x = drift(rx[i], vx[i], ax[i], dt, half_dt2);
+            const double y = drift(ry[i], vy[i], ay[i], dt, half_dt2);
+            const double z = drift(rz[i], vz[i], az[i], dt, half_dt2);
+            if (f64) static_cast<double4 *>(dst)[i] = stage_value<double4>(x, y, z, p);
+            else static_cast<float4 *>(dst)[i] = stage_value<float4>(x, y, z, p);
+        } else {
+            if (f64) static_cast<double4 *>(dst)[i] = make_double4(1e18, 1e18, 1e18, 0.0);
+            else static_cast<float4 *>(dst)[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        }
+    }
+}
+
+constexpr int kMomThreads = 256;
+
+// Fixed-shape tree over the block: identical summation order on every run.
+__device__ void block_sum(double *sh, int k, double v)
+{
+    sh[k * kMomThreads + threadIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kMomThreads)
+    moments_kernel(int pass, int n, const double *__restrict__ x, const double *__restrict__ y,
+                   const double *__restrict__ z, const double *__restrict__ vx,
+                   const double *__restrict__ vy, const double *__restrict__ vz, double cx,
+                   double cy, double cz, double *partials)
+{
+    __shared__ double sh[kMomSlots * kMomThreads];
+    double acc[kMomSlots];
+    for (int k = 0; k < kMomSlots; ++k) acc[k] = 0.0;
+    acc[10] = -INFINITY;
+    acc[11] = -INFINITY;
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk;
+    const int hi = min(n, lo + chunk);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        if (pass == 0) {
+            acc[0] += x[i];
+            acc[1] += y[i];
+            acc[2] += z[i];
+        } else if (pass == 1) {
+            const double dx = x[i] - cx, dy = y[i] - cy, dz = z[i] - cz;
+            acc[0] += dx * dx + dy * dy + dz * dz;
+            acc[1] += vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+            acc[2] += vx[i];
+            acc[3] += vy[i];
+            acc[4] += vz[i];
+            acc[5] += x[i] * x[i];
+            acc[6] += vx[i] * vx[i];
+            acc[7] += x[i] * vx[i];
+            acc[10] = fmax(acc[10], x[i]);
+            acc[11] = fmax(acc[11], vx[i]);
+        } else {
+            acc[0] += x[i];
+        }
+    }
+    for (int k = 0; k < kMomSlots; ++k) block_sum(sh, k, acc[k]);
+    __syncthreads();
+    for (int stride = kMomThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            for (int k = 0; k < kMomSlots; ++k) {
+                double *s = sh + k * kMomThreads;
+                s[threadIdx.x] = (k >= 10) ? fmax(s[threadIdx.x], s[threadIdx.x + stride])
+                                           : s[threadIdx.x] + s[threadIdx.x + stride];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kMomSlots)
+        partials[blockIdx.x * kMomSlots + threadIdx.x] = sh[threadIdx.x * kMomThreads];
+}
+
+__global__ void moments_finish_kernel(const double *__restrict__ partials, int nblocks,
+                                      double *out)
+{
+    const int k = threadIdx.x;
+    if (k >= kMomSlots) return;
+    double acc = (k >= 10) ? -INFINITY : 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = partials[b * kMomSlots + k];
+        acc = (k >= 10) ? fmax(acc, v) : acc + v;
+    }
+    out[k] = acc;
+}
+
+int grid_for(int n, int threads)
+{
+    int g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 4096) g = 4096;
+    return g;
+}
+
+}  // namespace
+
+cudaError_t launch_aos_to_soa(const double *in, int n, double *x, double *y, double *z, int *bad,
+                              cudaStream_t s)
+{
+    aos_to_soa_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, x, y, z, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z, int n,
+                              double *out, cudaStream_t s)
+{
+    soa_to_aos_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, z, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
+                         void *dst, bool f64, double cx, double cy, double cz, double inv_l0,
+                         cudaStream_t s)
+{
+    stage_kernel<<<grid_for(npad, 256), 256, 0, s>>>(x, y, z, n, npad, dst, f64 ? 1 : 0, cx, cy,
+                                                     cz, inv_l0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
+                               int npad, void *dst, bool f64, double dt, double half_dt2,
+                               double cx, double cy, double cz, double inv_l0, cudaStream_t s)
+{
+    stage_drift_kernel<<<grid_for(npad, 256), 256, 0, s>>>(r[0], r[1], r[2], v[0], v[1], v[2],
+                                                           a[0], a[1], a[2], n, npad, dst,
+                                                           f64 ? 1 : 0, dt, half_dt2, cx, cy, cz,
+                                                           inv_l0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int pass, int n, const double *x, const double *y, const double *z,
+                           const double *vx, const double *vy, const double *vz, double cx,
+                           double cy, double cz, double *block_partials, double *out,
+                           cudaStream_t s)
+{
+    moments_kernel<<<kMomBlocks, kMomThreads, 0, s>>>(pass, n, x, y, z, vx, vy, vz, cx, cy, cz,
+                                                      block_partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    moments_finish_kernel<<<1, 32, 0, s>>>(block_partials, kMomBlocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ppk

@@ -1,0 +1,289 @@
+"""GPU path vs the FP64 oracle, through the C ABI (ctypes binding).
+
+Tolerances: the force (field) relative L2 error must be <= 1e-5 against the FP64
+oracle for the FP32-pair paths, and <= 1e-12 for the all-FP64 path; per particle the
+error must stay below 1e-4 of the RMS field (an element-wise bound).  Run-level
+checks compare positions, displacements and velocities after a full run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_10640_gb300 import capi, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+ELEM_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    capi.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def check_fields(E, ref, tol=FORCE_TOL, elem=ELEM_TOL):
+    assert np.all(np.isfinite(E))
+    r = rel_l2(E, ref)
+    assert r <= tol, r
+    rms = np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
+    worst = np.max(np.linalg.norm(E - ref, axis=1)) / rms
+    assert worst <= elem, worst
+    return r
+
+
+def gpu_fields(pos, w, eps, acc=None, split=None, variant=None, dt=1e-15):
+    with capi.Simulation(pos.shape[0], w, dt, eps, acc=acc) as sim:
+        if split is not None:
+            sim.set_option(capi.PP_OPT_SPLIT, split)
+        if variant is not None:
+            sim.set_option(capi.PP_OPT_VARIANT, variant)
+        sim.load(pos)
+        return sim.fields()
+
+
+SIZES = [1, 2, 3, 63, 64, 65, 127, 128, 129, 1000, 1023, 1024, 1025, 2047, 4099, 5003]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("eps", [0.0, 2e-8])
+def test_fields_match_oracle(n, eps):
+    pos = wl.gaussian_bunch(n, 1e-6, seed=100 + n)
+    w = 3.0
+    E = gpu_fields(pos, w, eps)
+    if n == 1:
+        assert np.all(E == 0.0)
+        return
+    check_fields(E, oracle.fields(pos, w, eps))
+
+
+@pytest.mark.parametrize("acc", [capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN, capi.PP_ACC_FP64_FULL])
+@pytest.mark.parametrize("n", [777, 4099, 40000])
+def test_accumulator_modes(acc, n):
+    pos = wl.uniform_sphere(n, 20e-6, seed=7 + n)
+    eps = 1e-9
+    ref = oracle.fields(pos, 10.0, eps)
+    E = gpu_fields(pos, 10.0, eps, acc=acc)
+    tol = 1e-12 if acc == capi.PP_ACC_FP64_FULL else FORCE_TOL
+    check_fields(E, ref, tol=tol, elem=(1e-10 if acc == capi.PP_ACC_FP64_FULL else ELEM_TOL))
+
+
+@pytest.mark.parametrize("split", [1, 2, 7, 16])
+def test_split_counts_agree(split):
+    n = 9000
+    pos = wl.gaussian_bunch(n, 5e-6, seed=31)
+    ref = oracle.fields(pos, 2.0, 1e-9)
+    E = gpu_fields(pos, 2.0, 1e-9, split=split)
+    check_fields(E, ref)
+
+
+def test_every_fp32_variant():
+    n = 6000
+    pos = wl.gaussian_bunch(n, 5e-6, seed=32)
+    ref = oracle.fields(pos, 2.0, 0.0)
+    # variant indices of the FP64-fold FP32 kernels in the compiled table
+    for v in range(4):
+        check_fields(gpu_fields(pos, 2.0, 0.0, variant=v), ref)
+
+
+def test_bitwise_determinism():
+    pos = wl.gaussian_bunch(20000, 5e-6, seed=33)
+    a = gpu_fields(pos, 2.0, 1e-9, split=5)
+    b = gpu_fields(pos, 2.0, 1e-9, split=5)
+    assert np.array_equal(a, b)
+
+
+def test_coincident_particles_without_softening():
+    pos = wl.gaussian_bunch(300, 1e-6, seed=34)
+    pos[17] = pos[3]                  # two particles at the same place
+    E = gpu_fields(pos, 1.0, 0.0)
+    check_fields(E, oracle.fields(pos, 1.0, 0.0))
+
+
+def test_run_matches_oracle_cold_gaussian_2048():
+    """The 2048-electron cold Gaussian, no softening, dt = 1e-16 s, all 200 steps."""
+    b = wl.COLD_GAUSSIAN_2048
+    pos0 = b.positions()
+    vel0 = b.velocities()
+    p_ref, v_ref, a_ref = oracle.vv_run(pos0, vel0, None, b.w, b.eps, b.dt, b.steps)
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.load(pos0, vel0)
+        sim.step(b.steps)
+        p, v, a, step = sim.state()
+        d = sim.diagnostics()
+    assert step == b.steps
+    assert rel_l2(p - pos0, p_ref - pos0) <= FORCE_TOL
+    assert rel_l2(v, v_ref) <= FORCE_TOL
+    assert rel_l2(a, a_ref) <= FORCE_TOL
+    d_ref = oracle.diagnostics(p_ref, v_ref, b.w)
+    assert abs(d["rms_radius"] / d_ref["rms_radius"] - 1) <= 1e-5
+    # the radius growth itself, not only the radius, must agree
+    d0 = oracle.diagnostics(pos0, vel0, b.w)
+    growth_gpu = d["rms_radius"] - d0["rms_radius"]
+    growth_ref = d_ref["rms_radius"] - d0["rms_radius"]
+    assert abs(growth_gpu / growth_ref - 1) <= 1e-4
+
+
+def test_run_matches_oracle_softened_sphere():
+    n, R, w, eps = 3000, 10e-6, 200.0, 1e-8
+    pos0 = wl.uniform_sphere(n, R, seed=35)
+    K = wl.explosion_rate(n, w, R)
+    dt = 0.02 / math.sqrt(2 * K)
+    steps = 60
+    p_ref, v_ref, a_ref = oracle.vv_run(pos0, np.zeros_like(pos0), None, w, eps, dt, steps)
+    with capi.Simulation(n, w, dt, eps) as sim:
+        sim.load(pos0)
+        sim.step(steps)
+        p, v, a, _ = sim.state()
+    assert rel_l2(p - pos0, p_ref - pos0) <= FORCE_TOL
+    assert rel_l2(v, v_ref) <= FORCE_TOL
+
+
+def test_step_with_and_without_graphs_is_bitwise_equal():
+    b = wl.COLD_GAUSSIAN_2048
+    pos0 = b.positions()
+    out = []
+    for gb in (0, 8):
+        with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+            sim.set_option(capi.PP_OPT_GRAPH_BLOCK, gb)
+            sim.load(pos0)
+            sim.step(37)
+            out.append(sim.state())
+    for x, y in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(x, y)
+
+
+def test_diagnostics_match_oracle():
+    n, w, eps = 5000, 7.0, 1e-9
+    pos = wl.gaussian_bunch(n, 3e-6, seed=36) + np.array([1e-6, -2e-6, 0.5e-6])
+    vel = wl.gaussian_bunch(n, 1e5, seed=37)
+    with capi.Simulation(n, w, 1e-15, eps) as sim:
+        sim.load(pos, vel)
+        d = sim.diagnostics(with_pe=True)
+    ref = oracle.diagnostics(pos, vel, w)
+    for k in ("rms_radius", "ke", "emit_x", "x_rms", "vx_rms", "cx", "cy", "cz"):
+        assert abs(d[k] / ref[k] - 1) <= 1e-12, k
+    assert d["x_max"] == ref["x_max"] and d["vx_max"] == ref["vx_max"]
+    pscale = oracle.constants()["me"] * w * np.abs(vel).sum()
+    for k in ("px", "py", "pz"):
+        assert abs(d[k] - ref[k]) <= 1e-12 * pscale
+    pe = oracle.potential_energy(pos, w, eps)
+    assert abs(d["pe"] / pe - 1) <= FORCE_TOL
+
+
+def test_checkpoint_resume_is_bitwise():
+    n, w, eps, dt = 3000, 50.0, 1e-9, 2e-15
+    pos0 = wl.uniform_sphere(n, 5e-6, seed=38)
+    with capi.Simulation(n, w, dt, eps) as a:
+        a.load(pos0)
+        a.step(10)
+        p, v, acc, step = a.state()
+        a.step(15)
+        ref = a.state()
+    with capi.Simulation(n, w, dt, eps) as b:
+        b.set_state(p, v, acc, step)
+        b.step(15)
+        got = b.state()
+    assert got[3] == ref[3] == 25
+    for x, y in zip(got[:3], ref[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_momentum_conserved():
+    n, w, eps = 4000, 100.0, 1e-9
+    pos0 = wl.gaussian_bunch(n, 5e-6, seed=39)
+    K = wl.explosion_rate(n, w, 5e-6)
+    with capi.Simulation(n, w, 0.02 / math.sqrt(2 * K), eps) as sim:
+        sim.load(pos0)
+        sim.step(100)
+        d = sim.diagnostics(with_pe=False)
+        _, v = sim.particles()
+    pscale = oracle.constants()["me"] * w * np.linalg.norm(v, axis=1).sum()
+    assert math.sqrt(d["px"] ** 2 + d["py"] ** 2 + d["pz"] ** 2) <= 1e-7 * pscale
+
+
+def test_device_pointer_interface():
+    torch = pytest.importorskip("torch")
+    n = 2500
+    pos = wl.gaussian_bunch(n, 2e-6, seed=40)
+    ref = oracle.fields(pos, 4.0, 0.0)
+    pos_d = torch.tensor(pos, device="cuda", dtype=torch.float64)
+    out_d = torch.empty((n, 3), device="cuda", dtype=torch.float64)
+    with capi.Simulation(n, 4.0, 1e-15, 0.0) as sim:
+        sim.load(pos_d)
+        sim.fields(out_d)
+    check_fields(out_d.cpu().numpy(), ref)
+
+
+def test_invalid_arguments_and_states():
+    with pytest.raises(capi.PPError) as e:
+        capi.pp_create(0, 1.0, 1e-15, 0.0)
+    assert e.value.status == capi.PP_ERR_ARG
+    with pytest.raises(capi.PPError) as e:
+        capi.pp_create(10, 1.0, -1.0, 0.0)
+    assert e.value.status == capi.PP_ERR_ARG
+    with capi.Simulation(10, 1.0, 1e-15, 0.0) as sim:
+        with pytest.raises(capi.PPError) as e:
+            sim.step(1)
+        assert e.value.status == capi.PP_ERR_STATE
+        bad = np.zeros((10, 3))
+        bad[4, 1] = np.nan
+        with pytest.raises(capi.PPError) as e:
+            sim.load(bad)
+        assert e.value.status == capi.PP_ERR_ARG
+        with pytest.raises(capi.PPError) as e:
+            sim.set_option(12345, 1)
+        assert e.value.status == capi.PP_ERR_ARG
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    """A withheld tile copy makes the kernel's bounded waits run out: the call returns
+    PP_ERR_TIMEOUT (no fault, no hang) and the context works again after a reload."""
+    n = 3000
+    pos = wl.gaussian_bunch(n, 2e-6, seed=41)
+    with capi.Simulation(n, 1.0, 1e-15, 1e-9) as sim:
+        sim.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
+        sim.load(pos)
+        sim.set_option(capi.PP_OPT_TEST_SKIP_COPY, 1)
+        with pytest.raises(capi.PPError) as e:
+            sim.step(1)
+        assert e.value.status == capi.PP_ERR_TIMEOUT
+        with pytest.raises(capi.PPError) as e:
+            sim.step(1)
+        assert e.value.status == capi.PP_ERR_STATE
+        sim.load(pos)
+        check_fields(sim.fields(), oracle.fields(pos, 1.0, 1e-9))
+
+
+def test_gaussian_65536_sampled_forces():
+    """The 65536-particle bunch in the benchmark's launch plan: sampled forces vs oracle."""
+    b = wl.GAUSSIAN_65536
+    pos = b.positions()
+    idx = np.sort(np.unique((wl.uniform(77, 0, 1024) * b.n).astype(np.int64)))
+    ref = oracle.fields_subset(pos, b.w, b.eps, idx)
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.load(pos)
+        E = sim.fields()
+    check_fields(E[idx], ref)
+
+
+def test_sphere_1m_sampled_forces_both_accumulators():
+    """2^20 particles: 2048 sampled fields, FP64 fold and compensated FP32 fold."""
+    b = wl.SPHERE_1M
+    pos = b.positions()
+    idx = np.sort(np.unique((wl.uniform(78, 0, 2048) * b.n).astype(np.int64)))
+    ref = oracle.fields_subset(pos, b.w, b.eps, idx)
+    for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN):
+        with capi.Simulation(b.n, b.w, b.dt, b.eps, acc=acc) as sim:
+            sim.load(pos)
+            E = sim.fields()
+        check_fields(E[idx], ref)
