@@ -1,0 +1,318 @@
+"""Benchmark: pair-interactions per second of the fused force + Velocity-Verlet step.
+
+Workload: the cold Gaussian bunch of N = 65536 macro-electrons (1e8 electrons,
+w = 1525.88), sigma = 10 um per coordinate, softening 1 nm, dt = 1e-14 s; seeded,
+synthetic.  One "step" is one time step of the whole hot path: the O(N^2) force sum
+(FP32 pairs, FP64 fold) with the push fused into its epilogue.  Throughput counts
+N^2 pair interactions per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+library's stream with a 256 MiB L2-flush write before it (outside the events).  Under
+torchrun each rank runs its own bunch (weak scaling, no data-path collective); rank 0
+prints one JSON line with the max time over ranks.  ``--impl reference`` times the
+FP64 CPU oracle instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2502_10640_gb300 import workloads as wl
+
+METRIC = "G pair-interactions/s & % FP32 peak; served p50/p99 latency at force rel-L2<=1e-5"
+UNIT = "Gpair-interactions/s"
+FLOP_PER_PAIR = 20          # counting convention for the FP32 roofline
+WORKLOAD = wl.GAUSSIAN_65536
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA pipe: 128 lanes per SM, 2 flop per FMA."""
+    return 2.0 * 128 * sms * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float, bunch=WORKLOAD):
+    """The FP64 oracle on this host's cores: fields at a bounded sample of targets
+    against all N sources (pair-interactions per second)."""
+    import oracle
+    pos = bunch.positions()
+    n = bunch.n
+    cores = os.cpu_count() or 1
+    m = 256
+    idx = np.arange(m, dtype=np.int64) * (n // m)
+    t0 = time.perf_counter()
+    oracle.fields_subset(pos, bunch.w, bunch.eps, idx)
+    first = time.perf_counter() - t0
+    rate = m * n / max(first, 1e-9)
+    m2 = int(min(n, max(m, rate * seconds / n)))
+    idx = np.linspace(0, n - 1, m2).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.fields_subset(pos, bunch.w, bunch.eps, idx)
+    el = time.perf_counter() - t0
+    return {"value": m2 * n / el / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"FP64 oracle fields at {m2} of {n} particles against all {n} sources "
+                      f"({m2 * n:.3e} pairs, {el:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    b = WORKLOAD
+    pos = b.positions()
+    n = b.n
+    m = 128                                            # targets per sampled step
+    stride = n // m
+    for w in range(args.warmup):
+        oracle.fields_subset(pos, b.w, b.eps, np.arange(m, dtype=np.int64) * stride + w % stride)
+    t = 0.0
+    for k in range(args.steps):
+        idx = np.arange(m, dtype=np.int64) * stride + (k % stride)
+        t0 = time.perf_counter()
+        oracle.fields_subset(pos, b.w, b.eps, idx)
+        t += time.perf_counter() - t0
+    pairs = args.steps * m * n
+    value = pairs / t / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded cold Gaussian bunch)",
+        "config": {"workload": b.name, "N": n, "w": b.w, "eps_m": b.eps, "dt_s": b.dt,
+                   "sample_per_step": f"fields at {m} of {n} targets against all {n} sources"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: FP64 oracle fields at {m} of {n} targets "
+                                   f"against all {n} sources"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2502_10640_gb300 import capi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    capi.load()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    b = WORKLOAD
+    seed = b.seed + 1000 * rank
+    pos0 = wl.gaussian_bunch(b.n, b.scale, seed)
+    n = b.n
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    sim = capi.Simulation(n, b.w, b.dt, b.eps)
+    sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
+    sim.load(pos0)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                     # evict L2 (outside the events)
+            starts[k].record(stream)
+            sim.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    pairs = float(n) * n * args.steps * world
+    value = pairs / total_s / 1e9
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = [torch.empty((n, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        hp, hv, ha = (x.numpy() for x in pin)
+        p, v, a, step, frame = sim.state()
+        hp[:], hv[:], ha[:] = p, v, a
+        t_e2e = 0.0
+        for k in range(args.e2e_steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            sim.set_state(hp, hv, ha, step, frame)
+            sim.step(1)
+            capi.pp_get_state(sim.ctx, hp, hv, ha)
+            t_e2e += time.perf_counter() - t0
+            step += 1
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": float(n) * n * args.e2e_steps * world / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 3 * n * 3 * 8,
+               "api": "pp_set_state(host r,v,a) + pp_step(1) + pp_get_state(host r,v,a)"}
+
+    sim.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    csum = clocks.summary()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sms, max_mhz)
+    per_step_ms = 1e3 * total_s / args.steps
+    achieved = FLOP_PER_PAIR * float(n) * n / (per_step_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded cold Gaussian bunch)",
+        "config": {"workload": b.name, "N": n, "w": b.w, "eps_m": b.eps, "dt_s": b.dt,
+                   "precision": "FP32 pair math, FP64 per-particle fold, FP64 r/v/a",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "pct_fp32_peak": 100.0 * achieved / peak},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": f"{FLOP_PER_PAIR} flop per pair; peak = 2 x 128 FP32 lanes x {sms} SMs x "
+                             f"{max_mhz:.0f} MHz ({'sm_max_mhz of measured peaks file' if peak_src == 'measured' else 'fallback clock'})"},
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "clocks": csum,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

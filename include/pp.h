@@ -60,6 +60,18 @@ typedef enum {
     PP_ACC_FP64_FULL = 2  /* FP64 pair math and accumulation (comparison path, slow)        */
 } pp_acc;
 
+/* How staged source positions carry precision into the FP32 pair math
+ * (option PP_OPT_POSITIONS).  SINGLE rounds each staged coordinate to one
+ * float, so a separation d carries an absolute error of about 2^-24 |r|,
+ * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs.  SPLIT
+ * stages hi + lo floats (about 48 bits) and forms d = (hi_i - hi_j) +
+ * (lo_i - lo_j), exact in its hi part for close pairs, at six more FP32
+ * operations per pair.  SPLIT is available with PP_ACC_FP64FOLD. */
+typedef enum {
+    PP_POS_SINGLE = 0,    /* default */
+    PP_POS_SPLIT = 1
+} pp_positions;
+
 /* Option keys for pp_set_option. */
 enum {
     PP_OPT_ACC = 1,            /* value: a pp_acc                                              */
@@ -68,6 +80,7 @@ enum {
     PP_OPT_GRAPH_BLOCK = 4,    /* value: steps per captured CUDA graph (0 = plain launches)   */
     PP_OPT_TIMEOUT_NS = 5,     /* value: limit of each device-side wait in ns (default 1e9)   */
     PP_OPT_VARIANT = 6,        /* value: force-kernel variant index (-1 = automatic)          */
+    PP_OPT_POSITIONS = 7,      /* value: a pp_positions (FP32 pair paths only)                 */
     PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy, so
                                   its bounded waits expire and the call returns
                                   PP_ERR_TIMEOUT (tests the timeout path; no fault, no hang) */
@@ -133,16 +146,21 @@ pp_status pp_diagnostics(pp_ctx *ctx, pp_diag *out, int with_pe);
 pp_status pp_get_particles(pp_ctx *ctx, double *pos, double *vel, int on_device);
 
 /*
- * Checkpoint / resume.  pp_get_state copies r, v, a ([N][3] each) and the
- * step counter out; pp_set_state restores them exactly (no force pass), so
- * that stepping on from a restored state is bitwise identical to stepping
- * on without the round trip.  acc must be the acceleration that belongs to
- * pos (as pp_get_state returns it).
+ * Checkpoint / resume.  pp_get_state copies r, v, a ([N][3] each; any may be
+ * NULL), the step counter and the staging frame out; pp_set_state restores
+ * them exactly (no force pass).  The staging frame is 4 host doubles
+ * {cx, cy, cz, L0}: the centre and the power-of-two length about which
+ * positions are staged to FP32.  Passing the frame saved by pp_get_state makes
+ * stepping on from the restored state bitwise identical to stepping on
+ * without the round trip; frame = NULL chooses a fresh frame (centroid and
+ * RMS radius of pos), which changes results at the FP32 rounding level only.
+ * acc must be the acceleration that belongs to pos (as pp_get_state returns
+ * it).  Invalid frame (non-finite, L0 <= 0 or not a power of two) -> PP_ERR_ARG.
  */
 pp_status pp_get_state(pp_ctx *ctx, double *pos, double *vel, double *acc, int64_t *step,
-                       int on_device);
+                       double *frame, int on_device);
 pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const double *acc,
-                       int64_t step, int on_device);
+                       int64_t step, const double *frame, int on_device);
 
 /* Number of particles of the context. */
 pp_status pp_get_n(const pp_ctx *ctx, int64_t *n);

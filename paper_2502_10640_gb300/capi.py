@@ -35,6 +35,10 @@ PP_OPT_SPLIT = 3
 PP_OPT_GRAPH_BLOCK = 4
 PP_OPT_TIMEOUT_NS = 5
 PP_OPT_VARIANT = 6
+PP_OPT_POSITIONS = 7
+
+PP_POS_SINGLE = 0
+PP_POS_SPLIT = 1
 PP_OPT_TEST_SKIP_COPY = 99
 
 
@@ -75,8 +79,10 @@ SIGNATURES = [
     ("pp_step", ctypes.c_int, [_CTX, _I64]),
     ("pp_diagnostics", ctypes.c_int, [_CTX, ctypes.POINTER(pp_diag), ctypes.c_int]),
     ("pp_get_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
-    ("pp_get_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, ctypes.POINTER(_I64), ctypes.c_int]),
-    ("pp_set_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, _I64, ctypes.c_int]),
+    ("pp_get_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, ctypes.POINTER(_I64),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("pp_set_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, _I64, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_int]),
     ("pp_get_n", ctypes.c_int, [_CTX, ctypes.POINTER(_I64)]),
     ("pp_destroy", ctypes.c_int, [_CTX]),
     ("pp_last_error", ctypes.c_char_p, [_CTX]),
@@ -126,7 +132,9 @@ def _arg(x, n: int | None, writable: bool):
             x = x.numpy()
         else:
             if x.dtype != torch.float64 or not x.is_contiguous():
-                raise ValueError("device arrays must be contiguous float64")
+                if writable:
+                    raise ValueError("device output arrays must be contiguous float64")
+                x = x.to(torch.float64).contiguous()
             if n is not None and tuple(x.shape) not in ((n, 3),):
                 raise ValueError(f"expected shape ({n}, 3), got {tuple(x.shape)}")
             torch.cuda.current_stream(x.device).synchronize()
@@ -215,6 +223,7 @@ def pp_get_particles(ctx, pos=None, vel=None):
 
 
 def pp_get_state(ctx, pos=None, vel=None, acc=None):
+    """(pos, vel, acc, step, frame); frame = (cx, cy, cz, L0) of the FP32 staging."""
     n = pp_get_n(ctx)
     if pos is None and vel is None and acc is None:
         pos, vel, acc = (np.empty((n, 3)) for _ in range(3))
@@ -223,17 +232,19 @@ def pp_get_state(ctx, pos=None, vel=None, acc=None):
     a, oa, k3 = _arg(acc, n, True)
     on = _same_kind(*(o for o, x in ((op, pos), (ov, vel), (oa, acc)) if x is not None))
     step = _I64()
-    _check(load().pp_get_state(ctx, p, v, a, ctypes.byref(step), on), ctx)
-    return pos, vel, acc, step.value
+    frame = (ctypes.c_double * 4)()
+    _check(load().pp_get_state(ctx, p, v, a, ctypes.byref(step), frame, on), ctx)
+    return pos, vel, acc, step.value, tuple(frame)
 
 
-def pp_set_state(ctx, pos, vel, acc, step: int) -> None:
+def pp_set_state(ctx, pos, vel, acc, step: int, frame=None) -> None:
     n = pp_get_n(ctx)
     p, op, k1 = _arg(pos, n, False)
     v, ov, k2 = _arg(vel, n, False)
     a, oa, k3 = _arg(acc, n, False)
     on = _same_kind(op, ov, oa)
-    _check(load().pp_set_state(ctx, p, v, a, int(step), on), ctx)
+    fr = None if frame is None else (ctypes.c_double * 4)(*[float(x) for x in frame])
+    _check(load().pp_set_state(ctx, p, v, a, int(step), fr, on), ctx)
 
 
 def pp_destroy(ctx) -> None:
@@ -276,8 +287,8 @@ class Simulation:
     def state(self):
         return pp_get_state(self.ctx)
 
-    def set_state(self, pos, vel, acc, step):
-        pp_set_state(self.ctx, pos, vel, acc, step)
+    def set_state(self, pos, vel, acc, step, frame=None):
+        pp_set_state(self.ctx, pos, vel, acc, step, frame)
 
     def close(self):
         if self.ctx:

@@ -69,6 +69,7 @@ struct pp_ctx {
     double cx = 0, cy = 0, cz = 0, l0 = 1;
 
     int acc = PP_ACC_FP64FOLD;
+    int positions = PP_POS_SINGLE;
     int split_override = 0;
     int variant_override = -1;
     int graph_block = 16;
@@ -93,17 +94,27 @@ void drop_graphs(pp_ctx *c)
 
 bool f64_pairs(const pp_ctx *c) { return c->acc == PP_ACC_FP64_FULL; }
 
+// Staging layout the force kernels of this context read.
+int stage_kind(const pp_ctx *c)
+{
+    if (f64_pairs(c)) return STAGE_F64;
+    return c->positions == PP_POS_SPLIT ? STAGE_F32X2 : STAGE_F32;
+}
+
 // Pick the variant for a kind and N (or the override).
 const Variant *pick_variant(const pp_ctx *c, int kind)
 {
     int count = 0;
     const Variant *vs = variants(&count);
     if (kind == KIND_FORCE32 && c->variant_override >= 0 && c->variant_override < count &&
-        vs[c->variant_override].kind == KIND_FORCE32 && vs[c->variant_override].acc == c->acc)
+        vs[c->variant_override].kind == KIND_FORCE32 && vs[c->variant_override].acc == c->acc &&
+        vs[c->variant_override].stage == stage_kind(c))
         return &vs[c->variant_override];
     const char *want = nullptr;
     if (kind == KIND_FORCE64) want = "f64.full.t128r2k128";
     else if (kind == KIND_PHI32) want = c->n >= 32768 ? "phi32.fold64.t256r2k256" : "phi32.fold64.t128r1k128";
+    else if (c->positions == PP_POS_SPLIT)
+        want = c->n >= 32768 ? "f32split.fold64.t256r4k256" : "f32split.fold64.t128r2k128";
     else if (c->acc == PP_ACC_KAHAN) want = c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128";
     else if (c->n >= 32768) want = "f32.fold64.t256r4k256";
     else if (c->n >= 4096) want = "f32.fold64.t128r2k128";
@@ -256,18 +267,29 @@ pp_status force_pass(pp_ctx *c, int mode, const void *src, void *dst, double *ou
     return PP_OK;
 }
 
-pp_status stage_current(pp_ctx *c, void *dst, bool f64)
+pp_status stage_current(pp_ctx *c, void *dst, int kind)
 {
-    PP_CUDA(launch_stage(c->r[0], c->r[1], c->r[2], (int)c->n, c->npad, dst, f64, c->cx, c->cy,
+    PP_CUDA(launch_stage(c->r[0], c->r[1], c->r[2], (int)c->n, c->npad, dst, kind, c->cx, c->cy,
                          c->cz, 1.0 / c->l0, c->stream));
+    return PP_OK;
+}
+
+// The step epilogue writes staged entries i < n only, so the padding tail of
+// both ping-pong buffers must hold far-away weight-0 sources of the current
+// staging type before any step runs.
+pp_status pad_both(pp_ctx *c)
+{
+    for (int b = 0; b < 2; ++b)
+        PP_CUDA(launch_fill_padding(c->stage[b], (int)c->n, c->npad, stage_kind(c), c->stream));
     return PP_OK;
 }
 
 // Stage the pending positions drift(r_n, v_n, a_n) into stage[parity].
 pp_status restage_pending(pp_ctx *c)
 {
+    if (pp_status st = pad_both(c)) return st;
     PP_CUDA(launch_stage_drift(c->r, c->v, c->a, (int)c->n, c->npad, c->stage[c->parity],
-                               f64_pairs(c), c->dt, c->dt * c->dt / 2.0, c->cx, c->cy, c->cz,
+                               stage_kind(c), c->dt, c->dt * c->dt / 2.0, c->cx, c->cy, c->cz,
                                1.0 / c->l0, c->stream));
     PP_CUDA(cudaStreamSynchronize(c->stream));
     return PP_OK;
@@ -479,18 +501,26 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
     if (pp_status s = check_ctx(c)) return s;
     switch (key) {
     case PP_OPT_ACC:
-        if (value < PP_ACC_FP64FOLD || value > PP_ACC_FP64_FULL) return fail(PP_ERR_ARG, "bad acc mode");
-        if (value != c->acc) {
-            const bool was64 = f64_pairs(c);
-            c->acc = (int)value;
-            drop_graphs(c);
-            if (c->loaded && was64 != f64_pairs(c)) {
-                // the pending r_{n+1} is staged in the other precision: restage it
-                PP_CUDA(cudaSetDevice(c->device));
-                return restage_pending(c);
-            }
+    case PP_OPT_POSITIONS: {
+        if (key == PP_OPT_ACC && (value < PP_ACC_FP64FOLD || value > PP_ACC_FP64_FULL))
+            return fail(PP_ERR_ARG, "bad acc mode");
+        if (key == PP_OPT_POSITIONS && value != PP_POS_SINGLE && value != PP_POS_SPLIT)
+            return fail(PP_ERR_ARG, "bad positions mode");
+        const int new_acc = key == PP_OPT_ACC ? (int)value : c->acc;
+        const int new_pos = key == PP_OPT_POSITIONS ? (int)value : c->positions;
+        if (new_pos == PP_POS_SPLIT && new_acc == PP_ACC_KAHAN)
+            return fail(PP_ERR_ARG, "split positions are implemented with the FP64 fold only");
+        const int old_kind = stage_kind(c);
+        c->acc = new_acc;
+        c->positions = new_pos;
+        drop_graphs(c);
+        if (c->loaded && old_kind != stage_kind(c)) {
+            // the pending r_{n+1} is staged in the old layout: restage it
+            PP_CUDA(cudaSetDevice(c->device));
+            return restage_pending(c);
         }
         return PP_OK;
+    }
     case PP_OPT_STREAM:
         drop_graphs(c);
         c->stream = value ? reinterpret_cast<cudaStream_t>(value) : c->own_stream;
@@ -550,7 +580,9 @@ pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int
     if (st != PP_OK) return st;
     // a_0 = F(r_0) (needed by the first Eq. G); the epilogue stages r_1.
     c->parity = 0;
-    st = stage_current(c, c->stage[1], f64_pairs(c));
+    st = pad_both(c);
+    if (st != PP_OK) return st;
+    st = stage_current(c, c->stage[1], stage_kind(c));
     if (st != PP_OK) return st;
     st = force_pass(c, MODE_INIT, c->stage[1], c->stage[0], nullptr);
     if (st != PP_OK) return st;
@@ -562,7 +594,7 @@ pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int
 }
 
 pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const double *acc,
-                       int64_t step, int on_device)
+                       int64_t step, const double *frame, int on_device)
 {
     if (pp_status s = check_ctx(c)) return s;
     if (!pos || !vel || !acc) return fail(PP_ERR_ARG, "pos, vel and acc are required");
@@ -577,8 +609,20 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
     st = take_bad_input_flag(c, &bad);
     if (st != PP_OK) return st;
     if (bad) return fail(PP_ERR_ARG, "non-finite state");
-    st = choose_frame(c);
-    if (st != PP_OK) return st;
+    if (frame) {
+        if (!(std::isfinite(frame[0]) && std::isfinite(frame[1]) && std::isfinite(frame[2]) &&
+              std::isfinite(frame[3]) && frame[3] > 0))
+            return fail(PP_ERR_ARG, "invalid staging frame");
+        int e = 0;
+        if (std::frexp(frame[3], &e) != 0.5) return fail(PP_ERR_ARG, "frame scale must be a power of two");
+        c->cx = frame[0];
+        c->cy = frame[1];
+        c->cz = frame[2];
+        c->l0 = frame[3];
+    } else {
+        st = choose_frame(c);
+        if (st != PP_OK) return st;
+    }
     // stage r_{n+1} = Eq. G(r_n, v_n, a_n) exactly as the step epilogue would
     c->parity = 0;
     st = restage_pending(c);
@@ -589,7 +633,7 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
 }
 
 pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t *step,
-                       int on_device)
+                       double *frame, int on_device)
 {
     if (pp_status s = check_ctx(c)) return s;
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
@@ -599,13 +643,19 @@ pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t
     if (vel && (st = export_aos(c, c->v, vel, on_device)) != PP_OK) return st;
     if (acc && (st = export_aos(c, c->a, acc, on_device)) != PP_OK) return st;
     if (step) *step = c->step;
+    if (frame) {
+        frame[0] = c->cx;
+        frame[1] = c->cy;
+        frame[2] = c->cz;
+        frame[3] = c->l0;
+    }
     PP_CUDA(cudaStreamSynchronize(c->stream));
     return PP_OK;
 }
 
 pp_status pp_get_particles(pp_ctx *c, double *pos, double *vel, int on_device)
 {
-    return pp_get_state(c, pos, vel, nullptr, nullptr, on_device);
+    return pp_get_state(c, pos, vel, nullptr, nullptr, nullptr, on_device);
 }
 
 pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
@@ -616,7 +666,7 @@ pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
     PP_CUDA(cudaSetDevice(c->device));
     // stage the current r_n into the idle buffer; the pending r_{n+1} stays put
     void *scratch = c->stage[c->parity ^ 1];
-    pp_status st = stage_current(c, scratch, f64_pairs(c));
+    pp_status st = stage_current(c, scratch, stage_kind(c));
     if (st != PP_OK) return st;
     double *target = on_device ? E_out : c->aos;
     st = force_pass(c, MODE_FIELDS, scratch, nullptr, target);
@@ -700,7 +750,7 @@ pp_status pp_diagnostics(pp_ctx *c, pp_diag *d, int with_pe)
         // phi'_i = sum_{j != i} 1/sqrt(|d'|^2 + eps'^2); PE = 1/2 k e^2 w^2 / L0 * sum_i phi'_i
         // the potential pass always uses FP32 sources, staged into the idle buffer
         void *scratch = c->stage[c->parity ^ 1];
-        st = stage_current(c, scratch, false);
+        st = stage_current(c, scratch, STAGE_F32);
         if (st == PP_OK) st = force_pass(c, MODE_PHI, scratch, nullptr, c->phi);
         if (st != PP_OK) return st;
         st = check_device_errors(c, false);

@@ -79,29 +79,55 @@ __device__ __forceinline__ double kick(double v, double a_old, double a_new, dou
     return __dadd_rn(v, __dmul_rn(__dadd_rn(a_old, a_new), half_dt));
 }
 
-template <class E>
-__device__ __forceinline__ E stage_value(double x, double y, double z, const ForceArgs &p);
+// Staged source layouts.
+//  STAGE_F32:   float4 (x', y', z', 1) per particle, npad entries.
+//  STAGE_F32X2: float4 hi[npad] followed by float4 lo[npad], with
+//               hi = fl32(p') and lo = fl32(p' - hi): about 48 significant bits.
+//  STAGE_F64:   double4 (x', y', z', 1) per particle (FP64 pair math).
+// p' = (r - centre) / L0 with L0 a power of two, so the scaling is exact.
+// Padding entries (n <= i < npad) sit at 1e18 with weight 0.
+enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2 };
 
-template <>
-__device__ __forceinline__ float4 stage_value<float4>(double x, double y, double z,
-                                                      const ForceArgs &p)
+__device__ __forceinline__ double staged_coord(double x, double c, double inv_l0)
 {
-    return make_float4(__double2float_rn(__dmul_rn(__dsub_rn(x, p.cx), p.inv_l0)),
-                       __double2float_rn(__dmul_rn(__dsub_rn(y, p.cy), p.inv_l0)),
-                       __double2float_rn(__dmul_rn(__dsub_rn(z, p.cz), p.inv_l0)), 1.0f);
+    return __dmul_rn(__dsub_rn(x, c), inv_l0);
 }
 
-template <>
-__device__ __forceinline__ double4 stage_value<double4>(double x, double y, double z,
-                                                        const ForceArgs &p)
+template <int KIND>
+__device__ __forceinline__ void store_staged(void *dst, int npad, int i, double x, double y,
+                                             double z, double cx, double cy, double cz,
+                                             double inv_l0)
 {
-    return make_double4(__dmul_rn(__dsub_rn(x, p.cx), p.inv_l0),
-                        __dmul_rn(__dsub_rn(y, p.cy), p.inv_l0),
-                        __dmul_rn(__dsub_rn(z, p.cz), p.inv_l0), 1.0);
+    const double px = staged_coord(x, cx, inv_l0);
+    const double py = staged_coord(y, cy, inv_l0);
+    const double pz = staged_coord(z, cz, inv_l0);
+    if (KIND == STAGE_F64) {
+        static_cast<double4 *>(dst)[i] = make_double4(px, py, pz, 1.0);
+    } else {
+        const float hx = __double2float_rn(px), hy = __double2float_rn(py),
+                    hz = __double2float_rn(pz);
+        static_cast<float4 *>(dst)[i] = make_float4(hx, hy, hz, 1.0f);
+        if (KIND == STAGE_F32X2)
+            static_cast<float4 *>(dst)[(size_t)npad + i] =
+                make_float4(__double2float_rn(px - (double)hx), __double2float_rn(py - (double)hy),
+                            __double2float_rn(pz - (double)hz), 0.0f);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_padding(void *dst, int npad, int i)
+{
+    if (KIND == STAGE_F64) {
+        static_cast<double4 *>(dst)[i] = make_double4(1e18, 1e18, 1e18, 0.0);
+    } else {
+        static_cast<float4 *>(dst)[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        if (KIND == STAGE_F32X2)
+            static_cast<float4 *>(dst)[(size_t)npad + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 // Epilogue for particle i given its full FP64 sum (staged units).
-template <class E>
+template <int KIND>
 __device__ __forceinline__ void finish_particle(const ForceArgs &p, int i, double sx, double sy,
                                                 double sz)
 {
@@ -136,13 +162,15 @@ __device__ __forceinline__ void finish_particle(const ForceArgs &p, int i, doubl
             rn[c] = drift(p.r[c][i], p.v[c][i], an[c], p.dt, p.half_dt2);
         }
     }
-    static_cast<E *>(p.dst)[i] = stage_value<E>(rn[0], rn[1], rn[2], p);
+    store_staged<KIND>(p.dst, p.npad, i, rn[0], rn[1], rn[2], p.cx, p.cy, p.cz, p.inv_l0);
 }
 
-// Shared-memory ring + barriers of one CTA.
-template <class E, int TILE, int STAGES>
+// Shared-memory ring + barriers of one CTA.  With TWO, every stage holds a
+// second tile (the lo parts of split staging, read from src + npad).
+template <class E, int TILE, int STAGES, bool TWO = false>
 struct Ring {
     E *buf;
+    E *buf2;
     uint64_t *full;
     uint64_t *empty;
 };
@@ -165,18 +193,23 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64
 // Stream the CTA's j-tiles through the ring and call body(tile, j_first) for
 // each.  Returns false if a wait ran out; the value is uniform within each
 // warp.  On false the caller must run ring_drain before the CTA exits.
-template <class E, int T, int TILE, int STAGES, class Body>
-__device__ __forceinline__ bool run_tiles(const ForceArgs &p, const Ring<E, TILE, STAGES> &rg,
-                                          int j0, int ntiles, int &issued, int &seen, Body &&body)
+template <class E, int T, int TILE, int STAGES, bool TWO, class Body>
+__device__ __forceinline__ bool run_tiles(const ForceArgs &p,
+                                          const Ring<E, TILE, STAGES, TWO> &rg, int j0,
+                                          int ntiles, int &issued, int &seen, Body &&body)
 {
     const int tid = threadIdx.x;
     const E *src = static_cast<const E *>(p.src);
     constexpr uint32_t kBytes = TILE * sizeof(E);
     auto issue = [&](int t) {
         const int s = t % STAGES;
-        mbar_arrive_expect_tx(&rg.full[s], kBytes);
+        mbar_arrive_expect_tx(&rg.full[s], TWO ? 2 * kBytes : kBytes);
         const bool withhold = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
-        if (!withhold) bulk_g2s(rg.buf + s * TILE, src + j0 + (size_t)t * TILE, kBytes, &rg.full[s]);
+        if (!withhold) {
+            const size_t off = (size_t)j0 + (size_t)t * TILE;
+            bulk_g2s(rg.buf + s * TILE, src + off, kBytes, &rg.full[s]);
+            if (TWO) bulk_g2s(rg.buf2 + s * TILE, src + (size_t)p.npad + off, kBytes, &rg.full[s]);
+        }
     };
     if (tid == 0) {
         for (int t = 0; t < STAGES && t < ntiles; ++t) issue(t);
@@ -187,7 +220,7 @@ __device__ __forceinline__ bool run_tiles(const ForceArgs &p, const Ring<E, TILE
         const uint32_t ph = (t / STAGES) & 1;
         if (!warp_wait(&rg.full[s], ph, p.timeout_ns)) return false;
         if (tid == 0) seen = t + 1;
-        body(rg.buf + s * TILE, j0 + t * TILE);
+        body(rg.buf + s * TILE, TWO ? rg.buf2 + s * TILE : nullptr, j0 + t * TILE);
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&rg.empty[s]);
         if (tid < 32 && t + STAGES < ntiles) {   // warp 0: lane 0 refills the stage
@@ -208,9 +241,10 @@ __device__ __forceinline__ bool run_tiles(const ForceArgs &p, const Ring<E, TILE
 // After a failed wait: thread 0 waits (bounded) for copies it issued that
 // have not been observed complete, so no bulk copy still targets shared
 // memory when the CTA exits.
-template <class E, int TILE, int STAGES>
-__device__ __forceinline__ void ring_drain(const ForceArgs &p, const Ring<E, TILE, STAGES> &rg,
-                                           int issued, int seen, int ntiles)
+template <class E, int TILE, int STAGES, bool TWO>
+__device__ __forceinline__ void ring_drain(const ForceArgs &p,
+                                           const Ring<E, TILE, STAGES, TWO> &rg, int issued,
+                                           int seen, int ntiles)
 {
     if (threadIdx.x != 0) return;
     for (int t = seen; t < issued; ++t) {
@@ -222,20 +256,35 @@ __device__ __forceinline__ void ring_drain(const ForceArgs &p, const Ring<E, TIL
 
 // ---- pair loops ----------------------------------------------------------
 
+// Separation component.  Single staging: d = p_i - p_j.  Split staging:
+// d = (hi_i - hi_j) + (lo_i - lo_j); for a close pair the hi difference is
+// exact (Sterbenz), so d keeps about 48 significant bits of the positions.
+template <bool SPLIT>
+__device__ __forceinline__ float sep(float hi_i, float lo_i, float hi_j, float lo_j)
+{
+    if (SPLIT) return (hi_i - hi_j) + (lo_i - lo_j);
+    return hi_i - hi_j;
+}
+
 // Fast loop: TILE sources against R targets, no checks.
-template <int R, int TILE>
-__device__ __forceinline__ void tile_fast(const float4 *__restrict__ tile, const float (&xi)[R],
-                                          const float (&yi)[R], const float (&zi)[R], float eps2,
-                                          float (&fx)[R], float (&fy)[R], float (&fz)[R])
+template <int R, int TILE, bool SPLIT>
+__device__ __forceinline__ void tile_fast(const float4 *__restrict__ tile,
+                                          const float4 *__restrict__ tlo, const float (&xi)[R],
+                                          const float (&yi)[R], const float (&zi)[R],
+                                          const float (&xl)[R], const float (&yl)[R],
+                                          const float (&zl)[R], float eps2, float (&fx)[R],
+                                          float (&fy)[R], float (&fz)[R])
 {
 #pragma unroll 4
     for (int j = 0; j < TILE; ++j) {
         const float4 q = tile[j];
+        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SPLIT) l = tlo[j];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float dx = xi[r] - q.x;
-            const float dy = yi[r] - q.y;
-            const float dz = zi[r] - q.z;
+            const float dx = sep<SPLIT>(xi[r], xl[r], q.x, l.x);
+            const float dy = sep<SPLIT>(yi[r], yl[r], q.y, l.y);
+            const float dz = sep<SPLIT>(zi[r], zl[r], q.z, l.z);
             const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
             const float inv = rsqrt_sfu(s);
             const float inv3 = inv * inv * inv;
@@ -248,16 +297,19 @@ __device__ __forceinline__ void tile_fast(const float4 *__restrict__ tile, const
 
 // Safe loop for one target: pairs with s == 0 add nothing.  Same operations
 // in the same order as tile_fast for every other pair.
-template <int TILE>
-__device__ __noinline__ float3 tile_safe1(const float4 *__restrict__ tile, float x, float y,
-                                          float z, float eps2)
+template <int TILE, bool SPLIT>
+__device__ __noinline__ float3 tile_safe1(const float4 *__restrict__ tile,
+                                          const float4 *__restrict__ tlo, float x, float y,
+                                          float z, float xl, float yl, float zl, float eps2)
 {
     float ax = 0.f, ay = 0.f, az = 0.f;
     for (int j = 0; j < TILE; ++j) {
         const float4 q = tile[j];
-        const float dx = x - q.x;
-        const float dy = y - q.y;
-        const float dz = z - q.z;
+        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SPLIT) l = tlo[j];
+        const float dx = sep<SPLIT>(x, xl, q.x, l.x);
+        const float dy = sep<SPLIT>(y, yl, q.y, l.y);
+        const float dz = sep<SPLIT>(z, zl, q.z, l.z);
         const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         if (s > 0.f) {
             const float inv = rsqrt_sfu(s);
@@ -336,7 +388,9 @@ __device__ __forceinline__ void split_gather(const ForceArgs &p, int ib, double 
 }
 
 // ---- FP32 pair math, FP64 or compensated fold ------------------------------
-template <int T, int R, int TILE, int STAGES, int ACC, int MINB>
+// SPLIT selects the hi/lo staging (about 48-bit separations at +6 FP32
+// operations per pair); otherwise sources and targets are single floats.
+template <int T, int R, int TILE, int STAGES, int ACC, int MINB, bool SPLIT>
 __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
 {
     constexpr int BI = T * R;
@@ -352,7 +406,9 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
     const int j1 = min(j0 + p.jchunk, p.npad);
     const int ntiles = (j1 - j0) / TILE;
 
-    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), bar_full, bar_empty};
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw);
+    Ring<float4, TILE, STAGES, SPLIT> rg{ring, SPLIT ? ring + STAGES * TILE : nullptr, bar_full,
+                                         bar_empty};
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
@@ -364,7 +420,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
     __syncthreads();
 
     const float4 *src = static_cast<const float4 *>(p.src);
-    float xi[R], yi[R], zi[R];
+    float xi[R], yi[R], zi[R], xl[R], yl[R], zl[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r * T + tid;
@@ -373,6 +429,10 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
         xi[r] = q.x;
         yi[r] = q.y;
         zi[r] = q.z;
+        const float4 l = (SPLIT && i < p.n) ? src[(size_t)p.npad + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xl[r] = l.x;
+        yl[r] = l.y;
+        zl[r] = l.z;
     }
 
     double dx64[R], dy64[R], dz64[R];  // FP64 fold (ACC_FP64FOLD)
@@ -385,16 +445,17 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
     const float eps2 = p.eps2f;
 
     int issued = 0, seen = 0;
-    const bool ok = run_tiles<float4, T, TILE, STAGES>(
-        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, int) {
+    const bool ok = run_tiles<float4, T, TILE, STAGES, SPLIT>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int) {
             float fx[R], fy[R], fz[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) fx[r] = fy[r] = fz[r] = 0.f;
-            tile_fast<R, TILE>(tile, xi, yi, zi, eps2, fx, fy, fz);
+            tile_fast<R, TILE, SPLIT>(tile, tlo, xi, yi, zi, xl, yl, zl, eps2, fx, fy, fz);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (!isfinite(fx[r] + fy[r] + fz[r])) {
-                    const float3 f = tile_safe1<TILE>(tile, xi[r], yi[r], zi[r], eps2);
+                    const float3 f = tile_safe1<TILE, SPLIT>(tile, tlo, xi[r], yi[r], zi[r], xl[r],
+                                                             yl[r], zl[r], eps2);
                     fx[r] = f.x;
                     fy[r] = f.y;
                     fz[r] = f.z;
@@ -417,7 +478,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
     }
     __syncthreads();
     if (s_abort) {
-        ring_drain<float4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        ring_drain(p, rg, issued, seen, ntiles);
         return;
     }
     if (ACC == ACC_KAHAN) {
@@ -434,7 +495,8 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceArgs p)
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        finish_particle<float4>(p, i0 + r * T + tid, dx64[r], dy64[r], dz64[r]);
+        finish_particle<SPLIT ? STAGE_F32X2 : STAGE_F32>(p, i0 + r * T + tid, dx64[r], dy64[r],
+                                                         dz64[r]);
 }
 
 // ---- potential: phi'_i = sum_{j != i, s > 0} 1/sqrt(s), FP32 pairs, FP64 fold ----
@@ -454,7 +516,7 @@ __global__ void __launch_bounds__(T) phi_f32_kernel(const ForceArgs p)
     const int j1 = min(j0 + p.jchunk, p.npad);
     const int ntiles = (j1 - j0) / TILE;
 
-    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), bar_full, bar_empty};
+    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), nullptr, bar_full, bar_empty};
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
@@ -482,8 +544,8 @@ __global__ void __launch_bounds__(T) phi_f32_kernel(const ForceArgs p)
     for (int r = 0; r < R; ++r) acc[r] = dummy[r] = 0.0;
     const float eps2 = p.eps2f;
     int issued = 0, seen = 0;
-    const bool ok = run_tiles<float4, T, TILE, STAGES>(
-        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, int jfirst) {
+    const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int jfirst) {
             float f[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) f[r] = 0.f;
@@ -509,7 +571,7 @@ __global__ void __launch_bounds__(T) phi_f32_kernel(const ForceArgs p)
     }
     __syncthreads();
     if (s_abort) {
-        ring_drain<float4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        ring_drain(p, rg, issued, seen, ntiles);
         return;
     }
     if (p.nsplit > 1) {
@@ -517,7 +579,7 @@ __global__ void __launch_bounds__(T) phi_f32_kernel(const ForceArgs p)
         split_gather<T, R>(p, ib, acc, dummy, dummy, 1);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) finish_particle<float4>(p, i0 + r * T + tid, acc[r], 0.0, 0.0);
+    for (int r = 0; r < R; ++r) finish_particle<STAGE_F32>(p, i0 + r * T + tid, acc[r], 0.0, 0.0);
 }
 
 // ---- FP64 pair math and accumulation (comparison path) ---------------------
@@ -537,7 +599,8 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
     const int j1 = min(j0 + p.jchunk, p.npad);
     const int ntiles = (j1 - j0) / TILE;
 
-    Ring<double4, TILE, STAGES> rg{reinterpret_cast<double4 *>(smem_raw), bar_full, bar_empty};
+    Ring<double4, TILE, STAGES> rg{reinterpret_cast<double4 *>(smem_raw), nullptr, bar_full,
+                                   bar_empty};
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
@@ -561,8 +624,8 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
     }
     const double eps2 = p.eps2d;
     int issued = 0, seen = 0;
-    const bool ok = run_tiles<double4, T, TILE, STAGES>(
-        p, rg, j0, ntiles, issued, seen, [&](const double4 *tile, int) {
+    const bool ok = run_tiles<double4, T, TILE, STAGES, false>(
+        p, rg, j0, ntiles, issued, seen, [&](const double4 *tile, const double4 *, int) {
             for (int j = 0; j < TILE; ++j) {
                 const double4 q = tile[j];
 #pragma unroll
@@ -587,7 +650,7 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
     }
     __syncthreads();
     if (s_abort) {
-        ring_drain<double4, TILE, STAGES>(p, rg, issued, seen, ntiles);
+        ring_drain(p, rg, issued, seen, ntiles);
         return;
     }
     if (p.nsplit > 1) {
@@ -595,7 +658,8 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
         split_gather<T, R>(p, ib, ax, ay, az, 3);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) finish_particle<double4>(p, i0 + r * T + tid, ax[r], ay[r], az[r]);
+    for (int r = 0; r < R; ++r)
+        finish_particle<STAGE_F64>(p, i0 + r * T + tid, ax[r], ay[r], az[r]);
 }
 
 }  // namespace ppk

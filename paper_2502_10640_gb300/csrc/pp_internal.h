@@ -26,6 +26,7 @@ struct Variant {
     const char *name;
     int kind;
     int acc;      // Acc
+    int stage;    // StageKind of the sources it reads
     int T, R, tile, stages;
     const void *fn;
     size_t smem;  // dynamic shared memory bytes
@@ -46,13 +47,16 @@ cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z,
 // Stage FP64 positions into float4 (or double4) sources; entries n..npad-1
 // become padding (far away, weight 0).
 cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
-                         void *dst, bool f64, double cx, double cy, double cz, double inv_l0,
+                         void *dst, int stage_kind, double cx, double cy, double cz, double inv_l0,
                          cudaStream_t s);
+
+// Write the padding entries n..npad-1 of a staging buffer (far away, weight 0).
+cudaError_t launch_fill_padding(void *dst, int n, int npad, int stage_kind, cudaStream_t s);
 
 // Stage the next positions of Eq. G, drift(r, v, a), exactly as the step
 // epilogue stages them (used after a state is restored).
 cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
-                               int npad, void *dst, bool f64, double dt, double half_dt2,
+                               int npad, void *dst, int stage_kind, double dt, double half_dt2,
                                double cx, double cy, double cz, double inv_l0, cudaStream_t s);
 
 // Moments over n particles in a fixed reduction order.

@@ -9,18 +9,19 @@ namespace ppk {
 
 namespace {
 
-template <int T, int R, int TILE, int STAGES, int ACC, int MINB>
+template <int T, int R, int TILE, int STAGES, int ACC, int MINB, bool SPLIT = false>
 Variant make_f32(const char *name)
 {
-    return Variant{name, KIND_FORCE32, ACC, T, R, TILE, STAGES,
-                   reinterpret_cast<const void *>(&force_f32_kernel<T, R, TILE, STAGES, ACC, MINB>),
-                   (size_t)STAGES * TILE * sizeof(float4)};
+    return Variant{name, KIND_FORCE32, ACC, SPLIT ? STAGE_F32X2 : STAGE_F32, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(
+                       &force_f32_kernel<T, R, TILE, STAGES, ACC, MINB, SPLIT>),
+                   (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1)};
 }
 
 template <int T, int R, int TILE, int STAGES>
 Variant make_phi(const char *name)
 {
-    return Variant{name, KIND_PHI32, ACC_FP64FOLD, T, R, TILE, STAGES,
+    return Variant{name, KIND_PHI32, ACC_FP64FOLD, STAGE_F32, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(&phi_f32_kernel<T, R, TILE, STAGES>),
                    (size_t)STAGES * TILE * sizeof(float4)};
 }
@@ -28,7 +29,7 @@ Variant make_phi(const char *name)
 template <int T, int R, int TILE, int STAGES>
 Variant make_f64(const char *name)
 {
-    return Variant{name, KIND_FORCE64, ACC_FP64FULL, T, R, TILE, STAGES,
+    return Variant{name, KIND_FORCE64, ACC_FP64FULL, STAGE_F64, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(&force_f64_kernel<T, R, TILE, STAGES>),
                    (size_t)STAGES * TILE * sizeof(double4)};
 }
@@ -40,6 +41,8 @@ const Variant kVariants[] = {
     make_f32<128, 1, 128, 4, ACC_FP64FOLD, 4>("f32.fold64.t128r1k128"),
     make_f32<256, 4, 256, 4, ACC_KAHAN, 2>("f32.kahan.t256r4k256"),
     make_f32<128, 2, 128, 4, ACC_KAHAN, 4>("f32.kahan.t128r2k128"),
+    make_f32<256, 4, 256, 4, ACC_FP64FOLD, 2, true>("f32split.fold64.t256r4k256"),
+    make_f32<128, 2, 128, 4, ACC_FP64FOLD, 4, true>("f32split.fold64.t128r2k128"),
     make_phi<256, 2, 256, 4>("phi32.fold64.t256r2k256"),
     make_phi<128, 1, 128, 4>("phi32.fold64.t128r1k128"),
     make_f64<128, 2, 128, 3>("f64.full.t128r2k128"),
@@ -94,53 +97,42 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ x, const double *__
     }
 }
 
+template <int KIND>
 __global__ void stage_kernel(const double *__restrict__ x, const double *__restrict__ y,
-                             const double *__restrict__ z, int n, int npad, void *dst, int f64,
-                             double cx, double cy, double cz, double inv_l0)
+                             const double *__restrict__ z, int n, int npad, void *dst, double cx,
+                             double cy, double cz, double inv_l0)
 {
-    ForceArgs p{};
-    p.cx = cx;
-    p.cy = cy;
-    p.cz = cz;
-    p.inv_l0 = inv_l0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-        if (f64) {
-            double4 *d = static_cast<double4 *>(dst);
-            d[i] = (i < n) ? stage_value<double4>(x[i], y[i], z[i], p)
-                           : make_double4(1e18, 1e18, 1e18, 0.0);
-        } else {
-            float4 *d = static_cast<float4 *>(dst);
-            d[i] = (i < n) ? stage_value<float4>(x[i], y[i], z[i], p)
-                           : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        }
+        if (i < n) store_staged<KIND>(dst, npad, i, x[i], y[i], z[i], cx, cy, cz, inv_l0);
+        else store_padding<KIND>(dst, npad, i);
     }
 }
 
+template <int KIND>
 __global__ void stage_drift_kernel(const double *__restrict__ rx, const double *__restrict__ ry,
                                    const double *__restrict__ rz, const double *__restrict__ vx,
                                    const double *__restrict__ vy, const double *__restrict__ vz,
                                    const double *__restrict__ ax, const double *__restrict__ ay,
                                    const double *__restrict__ az, int n, int npad, void *dst,
-                                   int f64, double dt, double half_dt2, double cx, double cy,
-                                   double cz, double inv_l0)
+                                   double dt, double half_dt2, double cx, double cy, double cz,
+                                   double inv_l0)
 {
-    ForceArgs p{};
-    p.cx = cx;
-    p.cy = cy;
-    p.cz = cz;
-    p.inv_l0 = inv_l0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
         if (i < n) {
-            const double x = drift(rx[i], vx[i], ax[i], dt, half_dt2);
-            const double y = drift(ry[i], vy[i], ay[i], dt, half_dt2);
-            const double z = drift(rz[i], vz[i], az[i], dt, half_dt2);
-            if (f64) static_cast<double4 *>(dst)[i] = stage_value<double4>(x, y, z, p);
-            else static_cast<float4 *>(dst)[i] = stage_value<float4>(x, y, z, p);
+            store_staged<KIND>(dst, npad, i, drift(rx[i], vx[i], ax[i], dt, half_dt2),
+                               drift(ry[i], vy[i], ay[i], dt, half_dt2),
+                               drift(rz[i], vz[i], az[i], dt, half_dt2), cx, cy, cz, inv_l0);
         } else {
-            if (f64) static_cast<double4 *>(dst)[i] = make_double4(1e18, 1e18, 1e18, 0.0);
-            else static_cast<float4 *>(dst)[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            store_padding<KIND>(dst, npad, i);
         }
     }
+}
+
+template <int KIND>
+__global__ void fill_padding_kernel(void *dst, int n, int npad)
+{
+    for (int i = n + blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x)
+        store_padding<KIND>(dst, npad, i);
 }
 
 constexpr int kMomThreads = 256;
@@ -240,22 +232,40 @@ cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z,
 }
 
 cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
-                         void *dst, bool f64, double cx, double cy, double cz, double inv_l0,
+                         void *dst, int kind, double cx, double cy, double cz, double inv_l0,
                          cudaStream_t s)
 {
-    stage_kernel<<<grid_for(npad, 256), 256, 0, s>>>(x, y, z, n, npad, dst, f64 ? 1 : 0, cx, cy,
-                                                     cz, inv_l0);
+    const int g = grid_for(npad, 256);
+    if (kind == STAGE_F32)
+        stage_kernel<STAGE_F32><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+    else if (kind == STAGE_F32X2)
+        stage_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+    else
+        stage_kernel<STAGE_F64><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_padding(void *dst, int n, int npad, int kind, cudaStream_t s)
+{
+    if (npad <= n) return cudaSuccess;
+    const int g = grid_for(npad - n, 256);
+    if (kind == STAGE_F32) fill_padding_kernel<STAGE_F32><<<g, 256, 0, s>>>(dst, n, npad);
+    else if (kind == STAGE_F32X2) fill_padding_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(dst, n, npad);
+    else fill_padding_kernel<STAGE_F64><<<g, 256, 0, s>>>(dst, n, npad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
-                               int npad, void *dst, bool f64, double dt, double half_dt2,
+                               int npad, void *dst, int kind, double dt, double half_dt2,
                                double cx, double cy, double cz, double inv_l0, cudaStream_t s)
 {
-    stage_drift_kernel<<<grid_for(npad, 256), 256, 0, s>>>(r[0], r[1], r[2], v[0], v[1], v[2],
-                                                           a[0], a[1], a[2], n, npad, dst,
-                                                           f64 ? 1 : 0, dt, half_dt2, cx, cy, cz,
-                                                           inv_l0);
+    const int g = grid_for(npad, 256);
+#define PP_SD_ARGS r[0], r[1], r[2], v[0], v[1], v[2], a[0], a[1], a[2], n, npad, dst, dt, half_dt2, \
+                   cx, cy, cz, inv_l0
+    if (kind == STAGE_F32) stage_drift_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    else if (kind == STAGE_F32X2) stage_drift_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    else stage_drift_kernel<STAGE_F64><<<g, 256, 0, s>>>(PP_SD_ARGS);
+#undef PP_SD_ARGS
     return cudaGetLastError();
 }
 

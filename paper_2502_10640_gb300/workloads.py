@@ -65,7 +65,7 @@ def gaussian(seed: int, stream: int, n: int) -> np.ndarray:
 
 
 def _recentre(pos: np.ndarray) -> np.ndarray:
-    return pos - pos.mean(axis=0, keepdims=True)
+    return np.ascontiguousarray(pos - pos.mean(axis=0, keepdims=True))
 
 
 def gaussian_bunch(n: int, sigma: float, seed: int) -> np.ndarray:
@@ -86,14 +86,14 @@ def uniform_sphere(n: int, radius: float, seed: int, recentre: bool = True) -> n
     sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
     r = radius * np.cbrt(u)
     pos = np.stack([r * sz * np.cos(ph), r * sz * np.sin(ph), r * cz], axis=1)
-    return _recentre(pos) if recentre else pos
+    return _recentre(pos) if recentre else np.ascontiguousarray(pos)
 
 
 def cube_lattice(n_side: int, side: float) -> np.ndarray:
     """[n_side^3][3] cell-centred lattice filling a cube of edge `side` centred at 0."""
     a = (np.arange(n_side, dtype=np.float64) + 0.5) * (side / n_side) - side / 2.0
     x, y, z = np.meshgrid(a, a, a, indexing="ij")
-    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    return np.ascontiguousarray(np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1))
 
 
 def lattice_weight(n0: float, side: float, n_particles: int) -> float:
