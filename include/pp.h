@@ -162,6 +162,33 @@ pp_status pp_get_state(pp_ctx *ctx, double *pos, double *vel, double *acc, int64
 pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const double *acc,
                        int64_t step, const double *frame, int on_device);
 
+/*
+ * pp_fields_noalloc -- the paper has no counterpart; this is a service entry
+ * point.  Field E_i (V/m) of Eq. B for N macro-electrons of weight w and
+ * softening eps at positions pos, written to E_out; both are [N][3] device
+ * memory of the current CUDA device, read and written on `stream` (a
+ * cudaStream_t, or NULL for the legacy default stream).  No context needed.
+ *
+ * It allocates nothing, for callers that may not call cudaMalloc (code that
+ * runs inside a memory arena owned by a host framework, code that must not
+ * trigger the allocator's implicit synchronisation, plug-ins restricted to the
+ * buffers they are handed).  Every intermediate lives in one fixed device
+ * array of about 3.8 MB that each GPU loading this library holds until the
+ * process exits; N above PP_FIELDS_NOALLOC_MAX_N returns PP_ERR_ARG.
+ *
+ * All calls on a device share that array and it keeps the last call's
+ * contents (the call clears what must start at zero itself).  Calls whose work
+ * overlaps on the GPU race on it: serialise them.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress with that
+ * device current); make that first call before any stream capture.  The call
+ * synchronises `stream` before it returns.  Errors: PP_ERR_ARG (size, null
+ * pointer, non-finite input), PP_ERR_TIMEOUT, PP_ERR_CUDA; message via
+ * pp_last_error(NULL).
+ */
+#define PP_FIELDS_NOALLOC_MAX_N 16384
+pp_status pp_fields_noalloc(int64_t N, double w, double softening, const double *pos,
+                            double *E_out, void *stream);
+
 /* Number of particles of the context. */
 pp_status pp_get_n(const pp_ctx *ctx, int64_t *n);
 

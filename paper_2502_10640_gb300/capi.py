@@ -88,7 +88,10 @@ SIGNATURES = [
     ("pp_last_error", ctypes.c_char_p, [_CTX]),
     ("pp_version", ctypes.c_char_p, []),
     ("pp_pairs_per_step", ctypes.c_double, [_I64]),
+    ("pp_fields_noalloc", ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_double, _DP, _DP, _VP]),
 ]
+
+PP_FIELDS_NOALLOC_MAX_N = 16384
 
 
 def library_path() -> str:
@@ -250,6 +253,21 @@ def pp_set_state(ctx, pos, vel, acc, step: int, frame=None) -> None:
 def pp_destroy(ctx) -> None:
     if ctx:
         _check(load().pp_destroy(ctx))
+
+
+def pp_fields_noalloc(n: int, w: float, softening: float, pos, out, stream=None) -> None:
+    """Field [V/m] of n particles at device positions `pos` into device `out` ([n][3],
+    CUDA float64 tensors), using no device allocation (fixed scratch, n <= 16384).
+
+    `stream` is a torch.cuda.Stream (default: the current stream of pos's device)."""
+    import torch
+    for x in (pos, out):
+        if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+                and tuple(x.shape) == (n, 3)):
+            raise ValueError("pos and out must be contiguous CUDA float64 tensors of shape (n, 3)")
+    s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+    _check(load().pp_fields_noalloc(int(n), float(w), float(softening), pos.data_ptr(),
+                                     out.data_ptr(), s.cuda_stream))
 
 
 def pp_last_error(ctx=None) -> str:

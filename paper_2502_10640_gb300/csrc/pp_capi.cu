@@ -38,6 +38,8 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+void ppk::set_last_error(const char *msg) { g_last_error = msg; }
+
 struct pp_ctx {
     int64_t n = 0;
     int npad = 0;

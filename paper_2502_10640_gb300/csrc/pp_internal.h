@@ -32,6 +32,9 @@ struct Variant {
     size_t smem;  // dynamic shared memory bytes
 };
 
+// Record the message pp_last_error() returns on this thread.
+void set_last_error(const char *msg);
+
 // Table of compiled force-kernel variants.
 const Variant *variants(int *count);
 
