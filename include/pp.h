@@ -189,6 +189,58 @@ pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const 
 pp_status pp_fields_noalloc(int64_t N, double w, double softening, const double *pos,
                             double *E_out, void *stream);
 
+/*
+ * ---- Batch contexts: many independent bunches, one persistent launch per step.
+ *
+ * A batch holds up to 4096 bunches ("slots"), each with its own N, weight,
+ * time step, softening and state, and advances all of them together: every
+ * time step is one launch of a persistent kernel whose CTAs pull work items
+ * (bunch, block of 512 targets, chunk of 8192 sources) from a queue.  A
+ * bunch's tiling depends on its own N only, so its results are bitwise the
+ * same alone or in any mix.  Device memory is admitted against the budget
+ * given at creation (pp_batch_footprint says what one bunch takes).  Step
+ * blocks of PP_OPT_GRAPH_BLOCK steps (even; default 16) replay a captured
+ * CUDA graph.  Options: PP_OPT_STREAM, PP_OPT_GRAPH_BLOCK, PP_OPT_TIMEOUT_NS.
+ * Bunches use single FP32 staging and the FP64 fold (PP_ACC_FP64FOLD).
+ */
+typedef struct pp_batch pp_batch;
+
+/* Device bytes one bunch of N particles takes in a batch (a function of N only). */
+pp_status pp_batch_footprint(int64_t N, int64_t *bytes);
+
+/* Create an empty batch on the current device with a device-memory budget in bytes. */
+pp_status pp_batch_create(int64_t budget_bytes, pp_batch **out);
+
+pp_status pp_batch_set_option(pp_batch *b, int key, int64_t value);
+
+/*
+ * Add a bunch (copies pos and vel, [N][3]; vel may be NULL for v = 0), run its
+ * initial force pass, and return its slot index.  PP_ERR_NOMEM if its
+ * footprint exceeds the remaining budget (nothing is changed then).
+ * Slots of removed bunches are reused.  The bunch joins the next pp_batch_step.
+ */
+pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softening,
+                       const double *pos, const double *vel, int on_device, int *slot);
+
+/* Remove a bunch and return its memory to the budget. */
+pp_status pp_batch_remove(pp_batch *b, int slot);
+
+/* Advance every bunch in the batch by nsteps Velocity-Verlet steps. */
+pp_status pp_batch_step(pp_batch *b, int64_t nsteps);
+
+/* r, v, a ([N][3], any may be NULL) and the step counter of one bunch. */
+pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, double *acc,
+                             int64_t *step, int on_device);
+
+/* Moments of one bunch (as pp_diagnostics; pe is NaN). */
+pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *out);
+
+/* Active bunches, device bytes in use and the budget (any pointer may be NULL). */
+pp_status pp_batch_info(pp_batch *b, int64_t *active, int64_t *bytes_used, int64_t *budget);
+
+/* Free the batch and all its bunches.  NULL is accepted. */
+pp_status pp_batch_destroy(pp_batch *b);
+
 /* Number of particles of the context. */
 pp_status pp_get_n(const pp_ctx *ctx, int64_t *n);
 
@@ -197,6 +249,34 @@ pp_status pp_destroy(pp_ctx *ctx);
 
 /* Message for the last non-OK status on this thread (ctx may be NULL). */
 const char *pp_last_error(const pp_ctx *ctx);
+
+/*
+ * Name of compiled force-kernel variant `index` (for PP_OPT_VARIANT and for
+ * tuning tools), or NULL past the last one.  Names read
+ * "<pairs>.<fold>.t<threads>r<targets per thread>k<tile>", e.g.
+ * "f32x2.fold64.t256r4k256": packed FP32x2 pair math, FP64 fold, 256 threads,
+ * 4 targets per thread, 256-source tiles.
+ */
+const char *pp_variant_name(int index);
+
+/* Outcome of pp_autotune. */
+typedef struct {
+    int variant;         /* chosen force-kernel variant (see pp_variant_name)       */
+    int split;           /* chosen j-split count S (j-chunks per block of targets)  */
+    double ms_per_pass;  /* measured time of one force pass with that choice, ms    */
+    int candidates;      /* number of (variant, split) pairs that were timed        */
+} pp_tune_result;
+
+/*
+ * Autotuner: time every compiled force-kernel variant that fits the
+ * context's accumulation and positions modes, each with the launch planner's
+ * j-split count S and with S/2 and 2S, on the context's loaded particles, and
+ * keep the fastest pair as the context's PP_OPT_VARIANT and PP_OPT_SPLIT.
+ * Only force passes run (fields of the current positions into scratch): the
+ * particle state and step counter are untouched.  Takes a few hundred force
+ * passes at most; PP_ERR_STATE if no particles are loaded.  out may be NULL.
+ */
+pp_status pp_autotune(pp_ctx *ctx, pp_tune_result *out);
 
 /* Library version string. */
 const char *pp_version(void);

@@ -48,6 +48,11 @@ class PPError(RuntimeError):
         self.status = status
 
 
+class pp_tune_result(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("split", ctypes.c_int),
+                ("ms_per_pass", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class pp_diag(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_int64),
                 ("rms_radius", ctypes.c_double), ("ke", ctypes.c_double), ("pe", ctypes.c_double),
@@ -87,7 +92,22 @@ SIGNATURES = [
     ("pp_destroy", ctypes.c_int, [_CTX]),
     ("pp_last_error", ctypes.c_char_p, [_CTX]),
     ("pp_version", ctypes.c_char_p, []),
+    ("pp_variant_name", ctypes.c_char_p, [ctypes.c_int]),
     ("pp_pairs_per_step", ctypes.c_double, [_I64]),
+    ("pp_autotune", ctypes.c_int, [_CTX, ctypes.POINTER(pp_tune_result)]),
+    ("pp_batch_footprint", ctypes.c_int, [_I64, ctypes.POINTER(_I64)]),
+    ("pp_batch_create", ctypes.c_int, [_I64, ctypes.POINTER(_CTX)]),
+    ("pp_batch_set_option", ctypes.c_int, [_CTX, ctypes.c_int, _I64]),
+    ("pp_batch_add", ctypes.c_int, [_CTX, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    _DP, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("pp_batch_remove", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("pp_batch_step", ctypes.c_int, [_CTX, _I64]),
+    ("pp_batch_get_state", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(_I64),
+                                          ctypes.c_int]),
+    ("pp_batch_diagnostics", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(pp_diag)]),
+    ("pp_batch_info", ctypes.c_int, [_CTX, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                     ctypes.POINTER(_I64)]),
+    ("pp_batch_destroy", ctypes.c_int, [_CTX]),
     ("pp_fields_noalloc", ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_double, _DP, _DP, _VP]),
 ]
 
@@ -163,6 +183,19 @@ def _same_kind(*ons):
 
 def pp_version() -> str:
     return load().pp_version().decode()
+
+
+def pp_variant_name(index: int):
+    name = load().pp_variant_name(int(index))
+    return name.decode() if name else None
+
+
+def variants() -> list[str]:
+    """Names of all compiled force-kernel variants, in index order."""
+    out = []
+    while (name := pp_variant_name(len(out))) is not None:
+        out.append(name)
+    return out
 
 
 def pp_pairs_per_step(n: int) -> float:
@@ -250,6 +283,14 @@ def pp_set_state(ctx, pos, vel, acc, step: int, frame=None) -> None:
     _check(load().pp_set_state(ctx, p, v, a, int(step), fr, on), ctx)
 
 
+def pp_autotune(ctx) -> dict:
+    """Time the fitting kernel variants and j-splits; keep the fastest on ctx."""
+    r = pp_tune_result()
+    _check(load().pp_autotune(ctx, ctypes.byref(r)), ctx)
+    return {"variant": r.variant, "variant_name": pp_variant_name(r.variant), "split": r.split,
+            "ms_per_pass": r.ms_per_pass, "candidates": r.candidates}
+
+
 def pp_destroy(ctx) -> None:
     if ctx:
         _check(load().pp_destroy(ctx))
@@ -275,6 +316,76 @@ def pp_last_error(ctx=None) -> str:
     return m.decode() if m else ""
 
 
+def pp_batch_footprint(n: int) -> int:
+    b = _I64()
+    _check(load().pp_batch_footprint(int(n), ctypes.byref(b)))
+    return b.value
+
+
+class Batch:
+    """Owning wrapper of a batch context (pp_batch_*): many bunches stepped together."""
+
+    def __init__(self, budget_bytes: int, graph_block: int | None = None):
+        self.b = _CTX()
+        _check(load().pp_batch_create(int(budget_bytes), ctypes.byref(self.b)))
+        if graph_block is not None:
+            self.set_option(PP_OPT_GRAPH_BLOCK, graph_block)
+
+    def set_option(self, key: int, value: int):
+        _check(load().pp_batch_set_option(self.b, int(key), int(value)))
+
+    def add(self, pos, w: float, dt: float, softening: float = 0.0, vel=None) -> int:
+        n = int(pos.shape[0])
+        p, op, k1 = _arg(pos, n, False)
+        v, ov, k2 = _arg(vel, n, False)
+        on = _same_kind(op, ov if vel is not None else None)
+        slot = ctypes.c_int()
+        _check(load().pp_batch_add(self.b, n, float(w), float(dt), float(softening), p, v, on,
+                                   ctypes.byref(slot)))
+        return slot.value
+
+    def remove(self, slot: int):
+        _check(load().pp_batch_remove(self.b, int(slot)))
+
+    def step(self, nsteps: int = 1):
+        _check(load().pp_batch_step(self.b, int(nsteps)))
+
+    def state(self, slot: int, n: int):
+        pos, vel, acc = (np.empty((n, 3)) for _ in range(3))
+        step = _I64()
+        _check(load().pp_batch_get_state(self.b, int(slot), pos.ctypes.data, vel.ctypes.data,
+                                         acc.ctypes.data, ctypes.byref(step), 0))
+        return pos, vel, acc, step.value
+
+    def diagnostics(self, slot: int) -> dict:
+        d = pp_diag()
+        _check(load().pp_batch_diagnostics(self.b, int(slot), ctypes.byref(d)))
+        return d.as_dict()
+
+    def info(self) -> dict:
+        a, u, g = _I64(), _I64(), _I64()
+        _check(load().pp_batch_info(self.b, ctypes.byref(a), ctypes.byref(u), ctypes.byref(g)))
+        return {"active": a.value, "bytes_used": u.value, "budget": g.value}
+
+    def close(self):
+        if self.b:
+            _check(load().pp_batch_destroy(self.b))
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Simulation:
     """Owning wrapper: one context, destroyed with the object or on close()."""
 
@@ -295,6 +406,9 @@ class Simulation:
 
     def step(self, nsteps: int = 1):
         pp_step(self.ctx, nsteps)
+
+    def autotune(self) -> dict:
+        return pp_autotune(self.ctx)
 
     def diagnostics(self, with_pe: bool = True) -> dict:
         return pp_diagnostics(self.ctx, with_pe)

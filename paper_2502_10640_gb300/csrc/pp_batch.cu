@@ -1,0 +1,574 @@
+// pp_batch.cu -- batch context: many independent bunches stepped together by
+// one persistent kernel launch per time step, admitted against a device-memory
+// budget, with CUDA-graph step blocks.  C ABI in include/pp.h (pp_batch_*).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+#include "pp_batch.cuh"
+#include "pp_internal.h"
+
+using namespace ppk;
+
+namespace {
+
+constexpr int kMaxBunches = 4096;
+
+pp_status bfail(pp_status s, const std::string &m)
+{
+    set_last_error(m.c_str());
+    return s;
+}
+
+pp_status bcuda(cudaError_t e, const char *where)
+{
+    return bfail(PP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define B_CUDA(call)                                       \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bcuda(e_, #call);    \
+    } while (0)
+
+struct Layout {
+    int npad, nib, nipad, nsplit, jchunk;
+    size_t state_bytes, stage_bytes, partial_bytes, ticket_bytes, total;
+};
+
+// Device bytes of one bunch; a function of N only.
+Layout layout_for(int64_t n)
+{
+    Layout L{};
+    L.npad = (int)((n + kPad - 1) / kPad * kPad);
+    L.nib = (int)((n + kBatchBI - 1) / kBatchBI);
+    L.nipad = L.nib * kBatchBI;
+    L.jchunk = kBatchJChunk;
+    L.nsplit = (L.npad + L.jchunk - 1) / L.jchunk;
+    L.state_bytes = (size_t)9 * L.npad * sizeof(double);
+    L.stage_bytes = (size_t)L.npad * sizeof(float4);
+    L.partial_bytes = L.nsplit > 1 ? (size_t)L.nsplit * 3 * L.nipad * sizeof(double) : 0;
+    L.ticket_bytes = (size_t)L.nib * sizeof(unsigned);
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    L.total = al(L.state_bytes) + 2 * al(L.stage_bytes) + al(L.partial_bytes) +
+              al(L.ticket_bytes) + al((size_t)3 * n * sizeof(double));
+    return L;
+}
+
+struct Slot {
+    bool active = false;
+    int64_t n = 0;
+    double w = 1, dt = 0, eps = 0;
+    Layout L{};
+    unsigned char *mem = nullptr;  // one allocation holding everything below
+    double *r[3] = {}, *v[3] = {}, *a[3] = {};
+    void *stage[2] = {};
+    double *partial = nullptr;
+    unsigned *tickets = nullptr;
+    double *aos = nullptr;         // [n][3] transfer scratch
+    int parity = 0;
+    int64_t step = 0;
+    double cx = 0, cy = 0, cz = 0, l0 = 1;
+};
+
+}  // namespace
+
+struct pp_batch {
+    int device = 0;
+    int sms = 0;
+    int grid = 0;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    int64_t budget = 0, used = 0;
+    std::vector<Slot> slots;
+    BunchDesc *d_descs = nullptr;     // [kMaxBunches]
+    BatchHeader *d_hdr = nullptr;
+    BunchDesc *d_init_desc = nullptr; // one bunch, for the initial force pass
+    BatchHeader *d_init_hdr = nullptr;
+    unsigned *d_queue = nullptr;
+    int *d_err = nullptr;             // [0] wait ran out, [1] non-finite input
+    double *mom_partials = nullptr, *mom_out = nullptr, *mom_host = nullptr;
+    bool dirty = true;
+    int graph_block = 16;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    uint64_t timeout_ns = 1000000000ull;
+    std::vector<int> order;           // active slots in table order
+};
+
+namespace {
+
+const void *batch_kernel()
+{
+    return reinterpret_cast<const void *>(
+        &batch_f32x2_kernel<kBatchT, kBatchR, kBatchTile, kBatchStages, kBatchMinB>);
+}
+
+size_t batch_smem()
+{
+    return (size_t)kBatchStages * kBatchTile * sizeof(float4) + (size_t)3 * kBatchBI * sizeof(double);
+}
+
+void drop_graph(pp_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
+}
+
+BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base)
+{
+    BunchDesc d{};
+    d.stage[0] = s.stage[0];
+    d.stage[1] = s.stage[1];
+    for (int c = 0; c < 3; ++c) {
+        d.r[c] = s.r[c];
+        d.v[c] = s.v[c];
+        d.a[c] = s.a[c];
+    }
+    d.partial = s.partial;
+    d.tickets = s.tickets;
+    d.n = (int)s.n;
+    d.npad = s.L.npad;
+    d.nib = s.L.nib;
+    d.nsplit = s.L.nsplit;
+    d.jchunk = s.L.jchunk;
+    d.nipad = s.L.nipad;
+    d.item_base = item_base;
+    d.parity0 = parity0;
+    d.mode = mode;
+    const double epsl = s.eps / s.l0;
+    d.eps2f = (float)(epsl * epsl);
+    d.cscale = kCoulomb * kE * kE * s.w / (kMe * s.l0 * s.l0);
+    d.dt = s.dt;
+    d.half_dt = s.dt / 2.0;
+    d.half_dt2 = s.dt * s.dt / 2.0;
+    d.cx = s.cx;
+    d.cy = s.cy;
+    d.cz = s.cz;
+    d.inv_l0 = 1.0 / s.l0;
+    return d;
+}
+
+pp_status launch_batch(pp_batch *b, const BunchDesc *descs, const BatchHeader *hdr, int step_k)
+{
+    B_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
+    const void *fn = batch_kernel();
+    int *err = b->d_err;
+    unsigned *queue = b->d_queue;
+    unsigned long long tmo = b->timeout_ns;
+    void *args[] = {(void *)&descs, (void *)&hdr, (void *)&queue, (void *)&step_k, (void *)&err,
+                    (void *)&tmo};
+    B_CUDA(cudaLaunchKernel(fn, dim3(b->grid), dim3(kBatchT), args, batch_smem(), b->stream));
+    return PP_OK;
+}
+
+pp_status read_errors(pp_batch *b, int *flags)
+{
+    B_CUDA(cudaMemcpyAsync(flags, b->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    if (flags[0] || flags[1]) B_CUDA(cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int), b->stream));
+    return PP_OK;
+}
+
+// Rewrite the device table of active bunches (table order = slot order).
+pp_status upload_table(pp_batch *b)
+{
+    std::vector<BunchDesc> h;
+    b->order.clear();
+    int items = 0;
+    for (int i = 0; i < (int)b->slots.size(); ++i) {
+        const Slot &s = b->slots[i];
+        if (!s.active) continue;
+        h.push_back(make_desc(s, MODE_STEP, s.parity, items));
+        b->order.push_back(i);
+        items += s.L.nib * s.L.nsplit;
+    }
+    BatchHeader hdr{(int)h.size(), items};
+    if (!h.empty())
+        B_CUDA(cudaMemcpyAsync(b->d_descs, h.data(), h.size() * sizeof(BunchDesc),
+                               cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    b->dirty = false;
+    return PP_OK;
+}
+
+pp_status slot_moments(pp_batch *b, Slot &s, int pass, double cx, double cy, double cz,
+                       double out[kMomSlots])
+{
+    B_CUDA(launch_moments(pass, (int)s.n, s.r[0], s.r[1], s.r[2], s.v[0], s.v[1], s.v[2], cx, cy,
+                          cz, b->mom_partials, b->mom_out, b->stream));
+    B_CUDA(cudaMemcpyAsync(b->mom_host, b->mom_out, kMomSlots * sizeof(double),
+                           cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    std::memcpy(out, b->mom_host, kMomSlots * sizeof(double));
+    return PP_OK;
+}
+
+pp_status check_slot(const pp_batch *b, int slot)
+{
+    if (!b) return bfail(PP_ERR_ARG, "null batch");
+    if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
+        return bfail(PP_ERR_ARG, "no such slot");
+    return PP_OK;
+}
+
+void free_slot(pp_batch *b, Slot &s)
+{
+    if (s.mem) cudaFree(s.mem);
+    b->used -= (int64_t)s.L.total;
+    s = Slot{};
+}
+
+}  // namespace
+
+extern "C" {
+
+pp_status pp_batch_footprint(int64_t N, int64_t *bytes)
+{
+    if (!bytes || N < 1 || N > (int64_t(1) << 28)) return bfail(PP_ERR_ARG, "bad N or null bytes");
+    *bytes = (int64_t)layout_for(N).total;
+    return PP_OK;
+}
+
+pp_status pp_batch_destroy(pp_batch *b)
+{
+    if (!b) return PP_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (auto &s : b->slots)
+        if (s.active) free_slot(b, s);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_hdr);
+    cudaFree(b->d_init_desc);
+    cudaFree(b->d_init_hdr);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_err);
+    cudaFree(b->mom_partials);
+    cudaFree(b->mom_out);
+    if (b->mom_host) cudaFreeHost(b->mom_host);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+    return PP_OK;
+}
+
+pp_status pp_batch_create(int64_t budget_bytes, pp_batch **out)
+{
+    if (!out) return bfail(PP_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (budget_bytes <= 0) return bfail(PP_ERR_ARG, "budget must be > 0");
+    pp_batch *b = new pp_batch();
+    b->budget = budget_bytes;
+    auto bail = [&](pp_status s, const char *m) {
+        pp_batch_destroy(b);
+        return bfail(s, m);
+    };
+    if (cudaGetDevice(&b->device) != cudaSuccess) return bail(PP_ERR_CUDA, "no CUDA device");
+    if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "cannot query SM count");
+    if (cudaFuncSetAttribute(batch_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem()) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "cannot configure the batch kernel");
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(), kBatchT, batch_smem()) !=
+            cudaSuccess || occ < 1)
+        return bail(PP_ERR_CUDA, "batch kernel does not fit on an SM");
+    b->grid = b->sms * occ;
+    if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "cudaStreamCreate failed");
+    b->stream = b->own_stream;
+    const bool ok = cudaMalloc(&b->d_descs, kMaxBunches * sizeof(BunchDesc)) == cudaSuccess &&
+                    cudaMalloc(&b->d_hdr, sizeof(BatchHeader)) == cudaSuccess &&
+                    cudaMalloc(&b->d_init_desc, sizeof(BunchDesc)) == cudaSuccess &&
+                    cudaMalloc(&b->d_init_hdr, sizeof(BatchHeader)) == cudaSuccess &&
+                    cudaMalloc(&b->d_queue, sizeof(unsigned)) == cudaSuccess &&
+                    cudaMalloc(&b->d_err, 2 * sizeof(int)) == cudaSuccess &&
+                    cudaMalloc(&b->mom_partials, kMomBlocks * kMomSlots * sizeof(double)) == cudaSuccess &&
+                    cudaMalloc(&b->mom_out, kMomSlots * sizeof(double)) == cudaSuccess &&
+                    cudaMallocHost(&b->mom_host, kMomSlots * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return bail(PP_ERR_NOMEM, "device allocation failed");
+    }
+    BatchHeader empty{0, 0};
+    if (cudaMemcpy(b->d_hdr, &empty, sizeof(empty), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, 2 * sizeof(int)) != cudaSuccess)
+        return bail(PP_ERR_CUDA, "initialisation failed");
+    *out = b;
+    return PP_OK;
+}
+
+pp_status pp_batch_set_option(pp_batch *b, int key, int64_t value)
+{
+    if (!b) return bfail(PP_ERR_ARG, "null batch");
+    switch (key) {
+    case PP_OPT_STREAM:
+        drop_graph(b);
+        b->stream = value ? reinterpret_cast<cudaStream_t>(value) : b->own_stream;
+        return PP_OK;
+    case PP_OPT_GRAPH_BLOCK:
+        if (value < 0 || value > 4096) return bfail(PP_ERR_ARG, "graph block must be in [0, 4096]");
+        drop_graph(b);
+        b->graph_block = (int)value;
+        return PP_OK;
+    case PP_OPT_TIMEOUT_NS:
+        if (value < 1000 || value > 60000000000ll) return bfail(PP_ERR_ARG, "timeout out of range");
+        drop_graph(b);
+        b->timeout_ns = (uint64_t)value;
+        return PP_OK;
+    default:
+        return bfail(PP_ERR_ARG, "option not supported by batch contexts");
+    }
+}
+
+pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softening,
+                       const double *pos, const double *vel, int on_device, int *slot_out)
+{
+    if (!b || !pos || !slot_out) return bfail(PP_ERR_ARG, "null argument");
+    if (N < 1 || N > (int64_t(1) << 28)) return bfail(PP_ERR_ARG, "N must be in [1, 2^28]");
+    if (!(std::isfinite(w) && w > 0) || !(std::isfinite(dt) && dt > 0) ||
+        !(std::isfinite(softening) && softening >= 0))
+        return bfail(PP_ERR_ARG, "w, dt must be finite and > 0; softening finite and >= 0");
+    B_CUDA(cudaSetDevice(b->device));
+    const Layout L = layout_for(N);
+    if (b->used + (int64_t)L.total > b->budget)
+        return bfail(PP_ERR_NOMEM, "the bunch does not fit in the remaining memory budget");
+    int idx = -1;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (!b->slots[i].active) {
+            idx = i;
+            break;
+        }
+    int nactive = 0;
+    for (auto &s : b->slots) nactive += s.active;
+    if (nactive >= kMaxBunches) return bfail(PP_ERR_NOMEM, "too many bunches");
+    if (idx < 0) {
+        idx = (int)b->slots.size();
+        b->slots.emplace_back();
+    }
+    Slot &s = b->slots[idx];
+    s = Slot{};
+    s.n = N;
+    s.w = w;
+    s.dt = dt;
+    s.eps = softening;
+    s.L = L;
+    if (cudaMalloc(&s.mem, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        s = Slot{};
+        return bfail(PP_ERR_NOMEM, "device allocation failed");
+    }
+    b->used += (int64_t)L.total;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    unsigned char *p = s.mem;
+    double *state = reinterpret_cast<double *>(p);
+    p += al(L.state_bytes);
+    for (int c = 0; c < 3; ++c) {
+        s.r[c] = state + (size_t)(0 + c) * L.npad;
+        s.v[c] = state + (size_t)(3 + c) * L.npad;
+        s.a[c] = state + (size_t)(6 + c) * L.npad;
+    }
+    s.stage[0] = p;
+    p += al(L.stage_bytes);
+    s.stage[1] = p;
+    p += al(L.stage_bytes);
+    s.partial = reinterpret_cast<double *>(p);
+    p += al(L.partial_bytes);
+    s.tickets = reinterpret_cast<unsigned *>(p);
+    p += al(L.ticket_bytes);
+    s.aos = reinterpret_cast<double *>(p);
+    s.active = true;
+    auto undo = [&](pp_status st, const std::string &m) {
+        free_slot(b, s);
+        return bfail(st, m);
+    };
+    const size_t bytes = (size_t)N * 3 * sizeof(double);
+    if (cudaMemsetAsync(state, 0, L.state_bytes, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(s.tickets, 0, L.ticket_bytes, b->stream) != cudaSuccess)
+        return undo(PP_ERR_CUDA, "memset failed");
+    const double *src = pos;
+    if (!on_device) {
+        if (cudaMemcpyAsync(s.aos, pos, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+            return undo(PP_ERR_CUDA, "copy of positions failed");
+        src = s.aos;
+    }
+    if (launch_aos_to_soa(src, (int)N, s.r[0], s.r[1], s.r[2], b->d_err + 1, b->stream) != cudaSuccess)
+        return undo(PP_ERR_CUDA, "layout conversion failed");
+    if (vel) {
+        const double *vs = vel;
+        if (!on_device) {
+            if (cudaMemcpyAsync(s.aos, vel, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+                return undo(PP_ERR_CUDA, "copy of velocities failed");
+            vs = s.aos;
+        }
+        if (launch_aos_to_soa(vs, (int)N, s.v[0], s.v[1], s.v[2], b->d_err + 1, b->stream) != cudaSuccess)
+            return undo(PP_ERR_CUDA, "layout conversion failed");
+    }
+    int flags[2] = {0, 0};
+    if (read_errors(b, flags) != PP_OK) return undo(PP_ERR_CUDA, "error word read failed");
+    if (flags[1]) return undo(PP_ERR_ARG, "non-finite position or velocity");
+    // staging frame of this bunch: its centroid and power-of-two RMS radius
+    double m[kMomSlots];
+    if (slot_moments(b, s, 0, 0, 0, 0, m) != PP_OK) return undo(PP_ERR_CUDA, "moments failed");
+    s.cx = m[0] / N;
+    s.cy = m[1] / N;
+    s.cz = m[2] / N;
+    if (slot_moments(b, s, 1, s.cx, s.cy, s.cz, m) != PP_OK) return undo(PP_ERR_CUDA, "moments failed");
+    const double rms = std::sqrt(m[0] / N);
+    s.l0 = 1.0;
+    if (std::isfinite(rms) && rms > 0) s.l0 = std::ldexp(1.0, std::max(-200, std::min(200, (int)std::lround(std::log2(rms)))));
+    // a_0 = F(r_0) with the batch kernel itself (identical tiling), staging r_1
+    if (launch_fill_padding(s.stage[0], (int)N, L.npad, STAGE_F32I, b->stream) != cudaSuccess ||
+        launch_stage(s.r[0], s.r[1], s.r[2], (int)N, L.npad, s.stage[1], STAGE_F32I, s.cx, s.cy,
+                     s.cz, 1.0 / s.l0, b->stream) != cudaSuccess)
+        return undo(PP_ERR_CUDA, "staging failed");
+    BunchDesc d = make_desc(s, MODE_INIT, 1, 0);
+    BatchHeader h{1, L.nib * L.nsplit};
+    if (cudaMemcpyAsync(b->d_init_desc, &d, sizeof(d), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_init_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return undo(PP_ERR_CUDA, "table upload failed");
+    if (launch_batch(b, b->d_init_desc, b->d_init_hdr, 0) != PP_OK)
+        return undo(PP_ERR_CUDA, "initial force pass failed to launch");
+    if (read_errors(b, flags) != PP_OK) return undo(PP_ERR_CUDA, "error word read failed");
+    if (flags[0]) return undo(PP_ERR_TIMEOUT, "a device-side wait ran out of time");
+    s.parity = 0;
+    s.step = 0;
+    b->dirty = true;
+    *slot_out = idx;
+    return PP_OK;
+}
+
+pp_status pp_batch_remove(pp_batch *b, int slot)
+{
+    if (pp_status st = check_slot(b, slot)) return st;
+    B_CUDA(cudaSetDevice(b->device));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    free_slot(b, b->slots[slot]);
+    b->dirty = true;
+    return PP_OK;
+}
+
+pp_status pp_batch_step(pp_batch *b, int64_t nsteps)
+{
+    if (!b) return bfail(PP_ERR_ARG, "null batch");
+    if (nsteps < 0) return bfail(PP_ERR_ARG, "nsteps must be >= 0");
+    B_CUDA(cudaSetDevice(b->device));
+    if (b->dirty) {
+        if (pp_status st = upload_table(b)) return st;
+    }
+    if (b->order.empty() || nsteps == 0) return PP_OK;
+    int64_t left = nsteps;
+    const int gb = b->graph_block;
+    if (gb > 0 && (gb % 2) == 0 && left >= gb && b->stream != nullptr) {
+        if (!b->graph || b->graph_steps != gb) {
+            drop_graph(b);
+            cudaGraph_t g = nullptr;
+            B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            pp_status st = PP_OK;
+            for (int k = 0; k < gb && st == PP_OK; ++k) st = launch_batch(b, b->d_descs, b->d_hdr, k);
+            cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (st != PP_OK) return st;
+            if (ce != cudaSuccess) return bcuda(ce, "cudaStreamEndCapture");
+            cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return bcuda(ie, "cudaGraphInstantiate");
+            b->graph_steps = gb;
+        }
+        while (left >= gb) {      // even blocks leave every bunch's parity unchanged
+            B_CUDA(cudaGraphLaunch(b->graph, b->stream));
+            left -= gb;
+        }
+    }
+    for (int64_t k = 0; k < left; ++k) {
+        if (pp_status st = launch_batch(b, b->d_descs, b->d_hdr, (int)k)) return st;
+    }
+    int flags[2] = {0, 0};
+    if (pp_status st = read_errors(b, flags)) return st;
+    if (flags[0]) {
+        // results of this call are void; restart the bunches from their last state is not
+        // possible, so the caller must re-add them
+        for (int i : b->order) b->slots[i].step = -1;
+        return bfail(PP_ERR_TIMEOUT, "a device-side wait ran out of time; bunch states are "
+                                     "unspecified and must be re-added");
+    }
+    for (int i : b->order) {
+        Slot &s = b->slots[i];
+        s.step += nsteps;
+        s.parity ^= (int)(left & 1);
+    }
+    if (left & 1) b->dirty = true;   // parity0 in the table changed
+    return PP_OK;
+}
+
+pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, double *acc,
+                             int64_t *step, int on_device)
+{
+    if (pp_status st = check_slot(b, slot)) return st;
+    B_CUDA(cudaSetDevice(b->device));
+    Slot &s = b->slots[slot];
+    if (s.step < 0) return bfail(PP_ERR_STATE, "bunch state is unspecified after a timeout");
+    double *const *arrs[3] = {s.r, s.v, s.a};
+    double *outs[3] = {pos, vel, acc};
+    const size_t bytes = (size_t)s.n * 3 * sizeof(double);
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        double *target = on_device ? outs[k] : s.aos;
+        B_CUDA(launch_soa_to_aos(arrs[k][0], arrs[k][1], arrs[k][2], (int)s.n, target, b->stream));
+        if (!on_device)
+            B_CUDA(cudaMemcpyAsync(outs[k], s.aos, bytes, cudaMemcpyDeviceToHost, b->stream));
+    }
+    if (step) *step = s.step;
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    return PP_OK;
+}
+
+pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *d)
+{
+    if (pp_status st = check_slot(b, slot)) return st;
+    if (!d) return bfail(PP_ERR_ARG, "out is null");
+    B_CUDA(cudaSetDevice(b->device));
+    Slot &s = b->slots[slot];
+    if (s.step < 0) return bfail(PP_ERR_STATE, "bunch state is unspecified after a timeout");
+    double m0[kMomSlots], m1[kMomSlots];
+    if (pp_status st = slot_moments(b, s, 0, 0, 0, 0, m0)) return st;
+    const double n = (double)s.n;
+    const double cx = m0[0] / n, cy = m0[1] / n, cz = m0[2] / n;
+    if (pp_status st = slot_moments(b, s, 1, cx, cy, cz, m1)) return st;
+    const double mw = kMe * s.w;
+    d->t = (double)s.step * s.dt;
+    d->step = s.step;
+    d->rms_radius = std::sqrt(m1[0] / n);
+    d->ke = 0.5 * mw * m1[1];
+    d->pe = NAN;
+    d->px = mw * m1[2];
+    d->py = mw * m1[3];
+    d->pz = mw * m1[4];
+    const double x2 = m1[5] / n, vx2 = m1[6] / n, xvx = m1[7] / n;
+    const double e2 = x2 * vx2 - xvx * xvx;
+    d->emit_x = std::sqrt(e2 > 0 ? e2 : 0.0);
+    d->x_rms = std::sqrt(x2);
+    d->x_max = m1[10];
+    d->vx_rms = std::sqrt(vx2);
+    d->vx_max = m1[11];
+    d->cx = cx;
+    d->cy = cy;
+    d->cz = cz;
+    return PP_OK;
+}
+
+pp_status pp_batch_info(pp_batch *b, int64_t *active, int64_t *bytes_used, int64_t *budget)
+{
+    if (!b) return bfail(PP_ERR_ARG, "null batch");
+    int64_t n = 0;
+    for (auto &s : b->slots) n += s.active;
+    if (active) *active = n;
+    if (bytes_used) *bytes_used = b->used;
+    if (budget) *budget = b->budget;
+    return PP_OK;
+}
+
+}  // extern "C"

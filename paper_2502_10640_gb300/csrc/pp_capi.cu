@@ -96,34 +96,48 @@ void drop_graphs(pp_ctx *c)
 
 bool f64_pairs(const pp_ctx *c) { return c->acc == PP_ACC_FP64_FULL; }
 
-// Staging layout the force kernels of this context read.
-int stage_kind(const pp_ctx *c)
-{
-    if (f64_pairs(c)) return STAGE_F64;
-    return c->positions == PP_POS_SPLIT ? STAGE_F32X2 : STAGE_F32;
-}
-
-// Pick the variant for a kind and N (or the override).
-const Variant *pick_variant(const pp_ctx *c, int kind)
+const Variant *variant_by_name(const char *want)
 {
     int count = 0;
     const Variant *vs = variants(&count);
-    if (kind == KIND_FORCE32 && c->variant_override >= 0 && c->variant_override < count &&
-        vs[c->variant_override].kind == KIND_FORCE32 && vs[c->variant_override].acc == c->acc &&
-        vs[c->variant_override].stage == stage_kind(c))
-        return &vs[c->variant_override];
-    const char *want = nullptr;
-    if (kind == KIND_FORCE64) want = "f64.full.t128r2k128";
-    else if (kind == KIND_PHI32) want = c->n >= 32768 ? "phi32.fold64.t256r2k256" : "phi32.fold64.t128r1k128";
-    else if (c->positions == PP_POS_SPLIT)
-        want = c->n >= 32768 ? "f32split.fold64.t256r4k256" : "f32split.fold64.t128r2k128";
-    else if (c->acc == PP_ACC_KAHAN) want = c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128";
-    else if (c->n >= 32768) want = "f32.fold64.t256r4k256";
-    else if (c->n >= 4096) want = "f32.fold64.t128r2k128";
-    else want = "f32.fold64.t128r1k128";
     for (int i = 0; i < count; ++i)
         if (std::strcmp(vs[i].name, want) == 0) return &vs[i];
     return &vs[0];
+}
+
+// The variant that runs this context's force passes: the override if it fits
+// the accumulation and positions modes, else the default for N.
+const Variant *force_variant(const pp_ctx *c)
+{
+    if (f64_pairs(c)) return variant_by_name("f64.full.t128r2k128");
+    int count = 0;
+    const Variant *vs = variants(&count);
+    if (c->variant_override >= 0 && c->variant_override < count) {
+        const Variant &v = vs[c->variant_override];
+        const bool split = v.stage == STAGE_F32X2;
+        if (v.kind == KIND_FORCE32 && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
+            return &v;
+    }
+    if (c->positions == PP_POS_SPLIT)
+        return variant_by_name(c->n >= 32768 ? "f32split.fold64.t256r4k256" : "f32split.fold64.t128r2k128");
+    if (c->acc == PP_ACC_KAHAN)
+        return variant_by_name(c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128");
+    // packed f32x2 pair math wherever there is enough work per CTA (defaults
+    // from GB300 measurements; pp_autotune refines them per device and N)
+    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k512m4");
+    if (c->n >= 2048) return variant_by_name("f32x2.fold64.t128r2k128");
+    return variant_by_name("f32.fold64.t128r1k128");
+}
+
+// Staging layout the force kernels of this context read.
+int stage_kind(const pp_ctx *c) { return force_variant(c)->stage; }
+
+// Pick the variant for a kind of pass.
+const Variant *pick_variant(const pp_ctx *c, int kind)
+{
+    if (kind == KIND_PHI32)
+        return variant_by_name(c->n >= 32768 ? "phi32.fold64.t256r2k256" : "phi32.fold64.t128r1k128");
+    return force_variant(c);
 }
 
 struct Plan {
@@ -154,7 +168,9 @@ Plan make_plan(pp_ctx *c, int kind)
         if (s_eff != s) continue;
         const int64_t ctas = (int64_t)pl.nib * s;
         const int64_t waves = (ctas + slots - 1) / slots;
-        const double cost = (double)waves * (chunk_tiles + 1.5);
+        // per-CTA set-up (targets, barriers, first copy) and the split
+        // epilogue cost about a quarter of a tile
+        const double cost = (double)waves * (chunk_tiles + 0.25);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
             best_s = s;
@@ -414,6 +430,13 @@ const char *pp_last_error(const pp_ctx *) { return g_last_error.c_str(); }
 
 double pp_pairs_per_step(int64_t N) { return (double)N * (double)N; }
 
+const char *pp_variant_name(int index)
+{
+    int count = 0;
+    const Variant *vs = variants(&count);
+    return (index >= 0 && index < count) ? vs[index].name : nullptr;
+}
+
 pp_status pp_get_n(const pp_ctx *c, int64_t *n)
 {
     if (!c || !n) return fail(PP_ERR_ARG, "null argument");
@@ -546,8 +569,13 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
         int count = 0;
         variants(&count);
         if (value < -1 || value >= count) return fail(PP_ERR_ARG, "no such variant");
+        const int old_kind = stage_kind(c);
         c->variant_override = (int)value;
         drop_graphs(c);
+        if (c->loaded && old_kind != stage_kind(c)) {
+            PP_CUDA(cudaSetDevice(c->device));
+            return restage_pending(c);
+        }
         return PP_OK;
     }
     case PP_OPT_TEST_SKIP_COPY:
@@ -705,6 +733,88 @@ pp_status pp_step(pp_ctx *c, int64_t nsteps)
     pp_status st = check_device_errors(c, true);
     if (st != PP_OK) return st;
     c->step += nsteps;
+    return PP_OK;
+}
+
+pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
+    PP_CUDA(cudaSetDevice(c->device));
+    int count = 0;
+    const Variant *vs = variants(&count);
+    const int saved_variant = c->variant_override, saved_split = c->split_override;
+    const int old_kind = stage_kind(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PP_CUDA(cudaEventCreate(&e0));
+    PP_CUDA(cudaEventCreate(&e1));
+    void *scratch = c->stage[c->parity ^ 1];
+    int best_v = -1, best_s = 0, tried = 0;
+    double best_ms = 1e300;
+    pp_status st = PP_OK;
+    for (int v = 0; v < count && st == PP_OK; ++v) {
+        const bool split_layout = vs[v].stage == STAGE_F32X2;
+        if (vs[v].kind != KIND_FORCE32 || vs[v].acc != c->acc ||
+            split_layout != (c->positions == PP_POS_SPLIT))
+            continue;
+        c->variant_override = v;
+        c->split_override = 0;
+        const Plan base = make_plan(c, KIND_FORCE32);
+        const int tiles = c->npad / vs[v].tile;
+        int cand[3] = {base.nsplit, std::max(1, base.nsplit / 2), std::min(tiles, 2 * base.nsplit)};
+        st = stage_current(c, scratch, vs[v].stage);
+        for (int k = 0; k < 3 && st == PP_OK; ++k) {
+            bool dup = false;
+            for (int q = 0; q < k; ++q) dup |= cand[q] == cand[k];
+            if (dup) continue;
+            c->split_override = cand[k];
+            // one untimed pass, then enough timed passes for about 5 ms (at least 2)
+            st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
+            if (st != PP_OK) break;
+            PP_CUDA(cudaEventRecord(e0, c->stream));
+            st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
+            PP_CUDA(cudaEventRecord(e1, c->stream));
+            PP_CUDA(cudaEventSynchronize(e1));
+            float first = 0.f;
+            PP_CUDA(cudaEventElapsedTime(&first, e0, e1));
+            const int reps = std::max(2, std::min(20, (int)(5.0 / std::max(first, 1e-3f))));
+            PP_CUDA(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < reps && st == PP_OK; ++r)
+                st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
+            PP_CUDA(cudaEventRecord(e1, c->stream));
+            PP_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            const double per = ms / reps;
+            ++tried;
+            if (per < best_ms) {
+                best_ms = per;
+                best_v = v;
+                best_s = cand[k];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == PP_OK) st = check_device_errors(c, false);
+    if (st != PP_OK || best_v < 0) {
+        c->variant_override = saved_variant;
+        c->split_override = saved_split;
+        return st != PP_OK ? st : fail(PP_ERR_STATE, "no variant fits the context's modes");
+    }
+    c->variant_override = best_v;
+    c->split_override = best_s;
+    drop_graphs(c);
+    if (old_kind != stage_kind(c)) {
+        st = restage_pending(c);
+        if (st != PP_OK) return st;
+    }
+    if (out) {
+        out->variant = best_v;
+        out->split = best_s;
+        out->ms_per_pass = best_ms;
+        out->candidates = tried;
+    }
     return PP_OK;
 }
 

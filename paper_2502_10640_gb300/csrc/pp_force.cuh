@@ -84,9 +84,22 @@ __device__ __forceinline__ double kick(double v, double a_old, double a_new, dou
 //  STAGE_F32X2: float4 hi[npad] followed by float4 lo[npad], with
 //               hi = fl32(p') and lo = fl32(p' - hi): about 48 significant bits.
 //  STAGE_F64:   double4 (x', y', z', 1) per particle (FP64 pair math).
+//  STAGE_F32I:  sources interleaved by pairs for packed f32x2 arithmetic: the
+//               32 bytes of pair k = (2k, 2k+1) hold x_2k x_2k+1 y_2k y_2k+1
+//               z_2k z_2k+1 w_2k w_2k+1 (same 16 bytes per source as STAGE_F32).
 // p' = (r - centre) / L0 with L0 a power of two, so the scaling is exact.
 // Padding entries (n <= i < npad) sit at 1e18 with weight 0.
-enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2 };
+enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2, STAGE_F32I = 3 };
+
+__device__ __forceinline__ void store_interleaved(void *dst, int i, float x, float y, float z,
+                                                  float w)
+{
+    float *f = static_cast<float *>(dst) + 8 * (size_t)(i >> 1) + (i & 1);
+    f[0] = x;
+    f[2] = y;
+    f[4] = z;
+    f[6] = w;
+}
 
 __device__ __forceinline__ double staged_coord(double x, double c, double inv_l0)
 {
@@ -103,6 +116,9 @@ __device__ __forceinline__ void store_staged(void *dst, int npad, int i, double 
     const double pz = staged_coord(z, cz, inv_l0);
     if (KIND == STAGE_F64) {
         static_cast<double4 *>(dst)[i] = make_double4(px, py, pz, 1.0);
+    } else if (KIND == STAGE_F32I) {
+        store_interleaved(dst, i, __double2float_rn(px), __double2float_rn(py),
+                          __double2float_rn(pz), 1.0f);
     } else {
         const float hx = __double2float_rn(px), hy = __double2float_rn(py),
                     hz = __double2float_rn(pz);
@@ -119,6 +135,8 @@ __device__ __forceinline__ void store_padding(void *dst, int npad, int i)
 {
     if (KIND == STAGE_F64) {
         static_cast<double4 *>(dst)[i] = make_double4(1e18, 1e18, 1e18, 0.0);
+    } else if (KIND == STAGE_F32I) {
+        store_interleaved(dst, i, 1e18f, 1e18f, 1e18f, 0.f);
     } else {
         static_cast<float4 *>(dst)[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
         if (KIND == STAGE_F32X2)
@@ -190,19 +208,30 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64
     return __all_sync(0xffffffffu, mine) != 0;
 }
 
-// Stream the CTA's j-tiles through the ring and call body(tile, j_first) for
-// each.  Returns false if a wait ran out; the value is uniform within each
+// Stream the CTA's j-tiles through the ring and call body(tile, tile_lo,
+// j_first) for each.  Lane 0 of warp 0 issues the bulk copies.  A stage is
+// refilled only after every warp has released it; the producer never blocks
+// for that while other tiles are ready to consume: after each tile it issues
+// whatever refills are already possible (non-blocking probe of the "empty"
+// barriers) and waits only when the very tile it needs next is not issued
+// yet.  Returns false if a wait ran out; the value is uniform within each
 // warp.  On false the caller must run ring_drain before the CTA exits.
+//
+// g0 is the number of tiles this CTA already streamed through the same ring
+// (persistent kernels run several work items back to back); ring slot and
+// barrier phase of local tile t follow from g = g0 + t.  Every earlier tile
+// must have been released by all warps before the call (a CTA-wide barrier).
 template <class E, int T, int TILE, int STAGES, bool TWO, class Body>
 __device__ __forceinline__ bool run_tiles(const ForceArgs &p,
                                           const Ring<E, TILE, STAGES, TWO> &rg, int j0,
-                                          int ntiles, int &issued, int &seen, Body &&body)
+                                          int ntiles, int &issued, int &seen, Body &&body,
+                                          int g0 = 0)
 {
     const int tid = threadIdx.x;
     const E *src = static_cast<const E *>(p.src);
     constexpr uint32_t kBytes = TILE * sizeof(E);
     auto issue = [&](int t) {
-        const int s = t % STAGES;
+        const int s = (g0 + t) % STAGES;
         mbar_arrive_expect_tx(&rg.full[s], TWO ? 2 * kBytes : kBytes);
         const bool withhold = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
         if (!withhold) {
@@ -211,28 +240,54 @@ __device__ __forceinline__ bool run_tiles(const ForceArgs &p,
             if (TWO) bulk_g2s(rg.buf2 + s * TILE, src + (size_t)p.npad + off, kBytes, &rg.full[s]);
         }
     };
+    // tile t may be issued once global tile g0 + t - STAGES has been released
+    auto released = [&](int t, bool block) {
+        const int u = g0 + t - STAGES;
+        if (u < 0) return true;
+        uint64_t *bar = &rg.empty[u % STAGES];
+        const uint32_t par = (u / STAGES) & 1;
+        return block ? mbar_wait_bounded(bar, par, p.timeout_ns) : mbar_test_wait(bar, par);
+    };
+    int next = 0;  // next local tile to issue (meaningful on thread 0 only)
+    int ok0 = 1;
     if (tid == 0) {
-        for (int t = 0; t < STAGES && t < ntiles; ++t) issue(t);
-        issued = ntiles < STAGES ? ntiles : STAGES;
+        for (; next < STAGES && next < ntiles; ++next) {
+            if (!released(next, true)) {
+                ok0 = 0;
+                break;
+            }
+            issue(next);
+        }
+        issued = next;
     }
+    if (tid < 32 && !__shfl_sync(0xffffffffu, ok0, 0)) return false;
     for (int t = 0; t < ntiles; ++t) {
-        const int s = t % STAGES;
-        const uint32_t ph = (t / STAGES) & 1;
+        const int g = g0 + t;
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        if (tid < 32) {  // warp 0: make sure tile t has been issued
+            int ok = 1;
+            if (tid == 0) {
+                while (ok && next <= t) {
+                    ok = released(next, true);
+                    if (ok) {
+                        issue(next);
+                        issued = ++next;
+                    }
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+        }
         if (!warp_wait(&rg.full[s], ph, p.timeout_ns)) return false;
         if (tid == 0) seen = t + 1;
         body(rg.buf + s * TILE, TWO ? rg.buf2 + s * TILE : nullptr, j0 + t * TILE);
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&rg.empty[s]);
-        if (tid < 32 && t + STAGES < ntiles) {   // warp 0: lane 0 refills the stage
-            int ok = 1;
-            if (tid == 0) {
-                ok = mbar_wait_bounded(&rg.empty[s], ph, p.timeout_ns) ? 1 : 0;
-                if (ok) {
-                    issue(t + STAGES);
-                    issued = t + STAGES + 1;
-                }
+        if (tid == 0) {  // refill every stage that is already free, without waiting
+            while (next < ntiles && released(next, false)) {
+                issue(next);
+                issued = ++next;
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
         }
     }
     return true;
@@ -244,13 +299,14 @@ __device__ __forceinline__ bool run_tiles(const ForceArgs &p,
 template <class E, int TILE, int STAGES, bool TWO>
 __device__ __forceinline__ void ring_drain(const ForceArgs &p,
                                            const Ring<E, TILE, STAGES, TWO> &rg, int issued,
-                                           int seen, int ntiles)
+                                           int seen, int ntiles, int g0 = 0)
 {
     if (threadIdx.x != 0) return;
     for (int t = seen; t < issued; ++t) {
         const bool withheld = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
         if (withheld) continue;
-        mbar_wait_bounded(&rg.full[t % STAGES], (t / STAGES) & 1, p.timeout_ns);
+        const int g = g0 + t;
+        mbar_wait_bounded(&rg.full[g % STAGES], (g / STAGES) & 1, p.timeout_ns);
     }
 }
 
@@ -660,6 +716,214 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
 #pragma unroll
     for (int r = 0; r < R; ++r)
         finish_particle<STAGE_F64>(p, i0 + r * T + tid, ax[r], ay[r], az[r]);
+}
+
+
+// ---- packed FP32x2 pair math (sm_100+ f32x2 instructions), FP64 fold --------
+// Sources are read two at a time from the interleaved layout, so one f32x2
+// instruction evaluates the same target against sources 2k and 2k+1; each
+// target keeps even-source and odd-source partial sums in the two lanes of its
+// accumulators and adds them at every fold.  Per pair: 5.5 f32x2 instructions
+// (11 FP32 lane operations, as in the scalar loop) and one SFU rsqrt, so the
+// FP32 work needs half the issue slots.
+typedef unsigned long long f2_t;   // two floats in one 64-bit register pair
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Scalar loop over an interleaved tile for one target: pairs with s == 0 add
+// nothing (the fallback when a packed tile sum is not finite).
+template <int TILE>
+__device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ tile, float x,
+                                                      float y, float z, float eps2)
+{
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int j = 0; j < TILE; ++j) {
+        const float *q = tile + 8 * (j >> 1) + (j & 1);
+        const float dx = x - q[0];
+        const float dy = y - q[2];
+        const float dz = z - q[4];
+        const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        if (s > 0.f) {
+            const float inv = rsqrt_sfu(s);
+            const float inv3 = inv * inv * inv;
+            ax = fmaf(inv3, dx, ax);
+            ay = fmaf(inv3, dy, ay);
+            az = fmaf(inv3, dz, az);
+        }
+    }
+    return make_float3(ax, ay, az);
+}
+
+// SMEM_ACC keeps the FP64 fold accumulators in shared memory (BI x 3 doubles
+// per CTA) instead of registers, trading a shared load/store per fold for
+// fewer registers and so more resident warps.
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false>
+__global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
+{
+    constexpr int BI = T * R;
+    static_assert(TILE % 2 == 0, "sources are consumed in pairs");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ int s_abort, s_flag;
+
+    const int tid = threadIdx.x;
+    const int ib = blockIdx.x % p.nib;
+    const int split = blockIdx.x / p.nib;
+    const int i0 = ib * BI;
+    const int j0 = split * p.jchunk;
+    const int j1 = min(j0 + p.jchunk, p.npad);
+    const int ntiles = (j1 - j0) / TILE;
+
+    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), nullptr, bar_full,
+                                  bar_empty};
+    // FP64 accumulators in shared memory follow the tile ring: [3][BI]
+    double *sacc = reinterpret_cast<double *>(smem_raw + (size_t)STAGES * TILE * sizeof(float4));
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], T / 32);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    if (SMEM_ACC) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            sacc[r * T + tid] = sacc[BI + r * T + tid] = sacc[2 * BI + r * T + tid] = 0.0;
+    }
+    __syncthreads();
+
+    const float *srcf = static_cast<const float *>(p.src);
+    f2_t X[R], Y[R], Z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        float x = -1e18f, y = -1e18f, z = -1e18f;  // targets past n: far from everything
+        if (i < p.n) {
+            const float *q = srcf + 8 * (size_t)(i >> 1) + (i & 1);
+            x = q[0];
+            y = q[2];
+            z = q[4];
+        }
+        X[r] = f2_pack(x, x);
+        Y[r] = f2_pack(y, y);
+        Z[r] = f2_pack(z, z);
+    }
+    double ax64[R], ay64[R], az64[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ax64[r] = ay64[r] = az64[r] = 0.0;
+    const f2_t EPS2 = f2_pack(p.eps2f, p.eps2f);
+
+    int issued = 0, seen = 0;
+    const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int) {
+            f2_t AX[R], AY[R], AZ[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
+#pragma unroll 2
+            for (int k = 0; k < TILE / 2; ++k) {
+                const float4 a = tile[2 * k];       // x0 x1 y0 y1
+                const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1
+                const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const f2_t DX = f2_sub(X[r], XJ);
+                    const f2_t DY = f2_sub(Y[r], YJ);
+                    const f2_t DZ = f2_sub(Z[r], ZJ);
+                    const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
+                    float s0, s1;
+                    f2_unpack(S, s0, s1);
+                    const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
+                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
+                    AX[r] = f2_fma(INV3, DX, AX[r]);
+                    AY[r] = f2_fma(INV3, DY, AY[r]);
+                    AZ[r] = f2_fma(INV3, DZ, AZ[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float x0, x1, y0, y1, z0, z1;
+                f2_unpack(AX[r], x0, x1);
+                f2_unpack(AY[r], y0, y1);
+                f2_unpack(AZ[r], z0, z1);
+                float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
+                if (!isfinite(fx + fy + fz)) {
+                    float xs, ys, zs, dummy;
+                    f2_unpack(X[r], xs, dummy);
+                    f2_unpack(Y[r], ys, dummy);
+                    f2_unpack(Z[r], zs, dummy);
+                    const float3 f = tile_safe1_interleaved<TILE>(
+                        reinterpret_cast<const float *>(tile), xs, ys, zs, p.eps2f);
+                    fx = f.x;
+                    fy = f.y;
+                    fz = f.z;
+                }
+                if (SMEM_ACC) {
+                    sacc[r * T + tid] += (double)fx;
+                    sacc[BI + r * T + tid] += (double)fy;
+                    sacc[2 * BI + r * T + tid] += (double)fz;
+                } else {
+                    ax64[r] += (double)fx;
+                    ay64[r] += (double)fy;
+                    az64[r] += (double)fz;
+                }
+            }
+        });
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(p.err, 1);
+    }
+    __syncthreads();
+    if (s_abort) {
+        ring_drain(p, rg, issued, seen, ntiles);
+        return;
+    }
+    if (SMEM_ACC) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            ax64[r] = sacc[r * T + tid];
+            ay64[r] = sacc[BI + r * T + tid];
+            az64[r] = sacc[2 * BI + r * T + tid];
+        }
+    }
+    if (p.nsplit > 1) {
+        if (!split_publish<T, R>(p, ib, split, ax64, ay64, az64, 3, &s_flag)) return;
+        split_gather<T, R>(p, ib, ax64, ay64, az64, 3);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        finish_particle<STAGE_F32I>(p, i0 + r * T + tid, ax64[r], ay64[r], az64[r]);
 }
 
 }  // namespace ppk

@@ -18,6 +18,16 @@ Variant make_f32(const char *name)
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1)};
 }
 
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false>
+Variant make_f32x2(const char *name)
+{
+    return Variant{name, KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(
+                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC>),
+                   (size_t)STAGES * TILE * sizeof(float4) +
+                       (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
+}
+
 template <int T, int R, int TILE, int STAGES>
 Variant make_phi(const char *name)
 {
@@ -35,14 +45,23 @@ Variant make_f64(const char *name)
 }
 
 const Variant kVariants[] = {
+    // scalar FP32 pair math (one source per instruction)
     make_f32<256, 4, 256, 4, ACC_FP64FOLD, 2>("f32.fold64.t256r4k256"),
-    make_f32<256, 8, 256, 4, ACC_FP64FOLD, 1>("f32.fold64.t256r8k256"),
     make_f32<128, 2, 128, 4, ACC_FP64FOLD, 4>("f32.fold64.t128r2k128"),
     make_f32<128, 1, 128, 4, ACC_FP64FOLD, 4>("f32.fold64.t128r1k128"),
     make_f32<256, 4, 256, 4, ACC_KAHAN, 2>("f32.kahan.t256r4k256"),
     make_f32<128, 2, 128, 4, ACC_KAHAN, 4>("f32.kahan.t128r2k128"),
     make_f32<256, 4, 256, 4, ACC_FP64FOLD, 2, true>("f32split.fold64.t256r4k256"),
     make_f32<128, 2, 128, 4, ACC_FP64FOLD, 4, true>("f32split.fold64.t128r2k128"),
+    // packed f32x2 pair math (two sources per instruction)
+    make_f32x2<256, 4, 256, 4, 2>("f32x2.fold64.t256r4k256"),
+    make_f32x2<128, 2, 128, 4, 4>("f32x2.fold64.t128r2k128"),
+    make_f32x2<256, 4, 512, 3, 2>("f32x2.fold64.t256r4k512"),
+    make_f32x2<128, 4, 512, 3, 4, true>("f32x2.sfold64.t128r4k512m4"),
+    make_f32x2<128, 4, 256, 4, 4, true>("f32x2.sfold64.t128r4k256m4"),
+    make_f32x2<128, 4, 512, 3, 5, true>("f32x2.sfold64.t128r4k512m5"),
+    make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
+    // potential (diagnostics) and all-FP64 comparison path
     make_phi<256, 2, 256, 4>("phi32.fold64.t256r2k256"),
     make_phi<128, 1, 128, 4>("phi32.fold64.t128r1k128"),
     make_f64<128, 2, 128, 3>("f64.full.t128r2k128"),
@@ -236,7 +255,9 @@ cudaError_t launch_stage(const double *x, const double *y, const double *z, int 
                          cudaStream_t s)
 {
     const int g = grid_for(npad, 256);
-    if (kind == STAGE_F32)
+    if (kind == STAGE_F32I)
+        stage_kernel<STAGE_F32I><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+    else if (kind == STAGE_F32)
         stage_kernel<STAGE_F32><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
     else if (kind == STAGE_F32X2)
         stage_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
@@ -249,7 +270,8 @@ cudaError_t launch_fill_padding(void *dst, int n, int npad, int kind, cudaStream
 {
     if (npad <= n) return cudaSuccess;
     const int g = grid_for(npad - n, 256);
-    if (kind == STAGE_F32) fill_padding_kernel<STAGE_F32><<<g, 256, 0, s>>>(dst, n, npad);
+    if (kind == STAGE_F32I) fill_padding_kernel<STAGE_F32I><<<g, 256, 0, s>>>(dst, n, npad);
+    else if (kind == STAGE_F32) fill_padding_kernel<STAGE_F32><<<g, 256, 0, s>>>(dst, n, npad);
     else if (kind == STAGE_F32X2) fill_padding_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(dst, n, npad);
     else fill_padding_kernel<STAGE_F64><<<g, 256, 0, s>>>(dst, n, npad);
     return cudaGetLastError();
@@ -262,7 +284,8 @@ cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *c
     const int g = grid_for(npad, 256);
 #define PP_SD_ARGS r[0], r[1], r[2], v[0], v[1], v[2], a[0], a[1], a[2], n, npad, dst, dt, half_dt2, \
                    cx, cy, cz, inv_l0
-    if (kind == STAGE_F32) stage_drift_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    if (kind == STAGE_F32I) stage_drift_kernel<STAGE_F32I><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    else if (kind == STAGE_F32) stage_drift_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else if (kind == STAGE_F32X2) stage_drift_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else stage_drift_kernel<STAGE_F64><<<g, 256, 0, s>>>(PP_SD_ARGS);
 #undef PP_SD_ARGS

@@ -139,10 +139,14 @@ def test_every_fp32_variant():
     n = 6000
     pos = wl.gaussian_bunch(n, 5e-6, seed=32)
     ref = oracle.fields(pos, 2.0, 0.0)
-    # variant indices of the FP64-fold FP32 kernels in the compiled table
+    # every FP64-fold kernel on single-float sources (scalar and packed f32x2)
     bound = bound_for(pos, 2.0, 0.0)
-    for v in range(4):
-        check_fields(gpu_fields(pos, 2.0, 0.0, variant=v), ref, bound=bound, report=f"variant={v}")
+    names = capi.variants()
+    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32.fold64", "f32x2."))]
+    assert len(chosen) >= 7
+    for v in chosen:
+        check_fields(gpu_fields(pos, 2.0, 0.0, variant=v), ref, bound=bound,
+                     report=f"variant={names[v]}")
 
 
 def test_bitwise_determinism():
@@ -264,6 +268,24 @@ def test_checkpoint_resume_is_bitwise():
     assert got[3] == ref[3] == 25
     for x, y in zip(got[:3], ref[:3]):
         assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_state_and_results():
+    n, w, eps = 20000, 30.0, 1e-9
+    pos = wl.gaussian_bunch(n, 5e-6, seed=42)
+    ref = oracle.fields_subset(pos, w, eps, np.arange(0, n, 97))
+    with capi.Simulation(n, w, 1e-15, eps) as sim:
+        sim.load(pos)
+        before = sim.state()
+        res = sim.autotune()
+        after = sim.state()
+        for x, y in zip(before[:3], after[:3]):
+            assert np.array_equal(x, y)
+        assert res["candidates"] >= 3 and res["ms_per_pass"] > 0
+        assert res["variant_name"].startswith(("f32.", "f32x2."))
+        E = sim.fields()
+        sim.step(3)
+    check_fields(E[::97], ref, report=f"autotuned {res['variant_name']} S={res['split']}")
 
 
 def test_momentum_conserved():
