@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=8,
+                    help="steps of the 64-bunch mix, batched and one bunch per launch (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the bounded serving trace (0 = skip)")
     return ap.parse_args()
 
 
@@ -57,6 +62,19 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float) -> float:
+    """Maximum of a host scalar over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def load_peaks():
@@ -178,6 +196,66 @@ def cpu_baseline(seconds: float, bunch=WORKLOAD):
                       f"({m2 * n:.3e} pairs, {el:.1f} s)"}
 
 
+def run_batched(steps: int):
+    """The 64-bunch mix (N log-uniform 1024-131072): one persistent launch per step for
+    all bunches, against the plain path that steps each bunch with its own launches."""
+    import torch
+    from paper_2502_10640_gb300 import capi
+    mix = wl.batch_mix()
+    pairs = float(sum(x.n ** 2 for x in mix)) * steps
+    with capi.Batch(150 << 30, graph_block=0) as bt:
+        for x in mix:
+            bt.add(x.positions(), x.w, x.dt, x.eps)
+        bt.step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt.step(steps)
+        t_batch = time.perf_counter() - t0
+    sims = []
+    try:
+        for x in mix:
+            s_ = capi.Simulation(x.n, x.w, x.dt, x.eps)
+            s_.set_option(capi.PP_OPT_GRAPH_BLOCK, 0)
+            s_.load(x.positions())
+            sims.append(s_)
+        for s_ in sims:
+            s_.step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for s_ in sims:
+                s_.step(1)
+        t_plain = time.perf_counter() - t0
+    finally:
+        for s_ in sims:
+            s_.close()
+    return {"workload": f"{len(mix)} cold bunches, N log-uniform 1024-131072 (sum N^2 = "
+                        f"{pairs / steps:.3e} per step), Gaussian/sphere 50/50",
+            "steps": steps, "unit": UNIT,
+            "batched": pairs / t_batch / 1e9,
+            "one_bunch_per_launch": pairs / t_plain / 1e9,
+            "speedup": t_plain / t_batch,
+            "timing": "host wall clock around the synchronous step calls"}
+
+
+def run_serving(count: int):
+    """Bounded serving trace: Poisson arrivals at 20 requests/s of uniform-sphere runs,
+    N and step counts scaled down (x1/8 and x1/20) so the run takes seconds."""
+    from paper_2502_10640_gb300 import serve
+    trace = wl.serve_trace(count)
+    reqs = serve.requests_from_trace(trace, n_scale=0.125, steps_scale=0.05)
+    srv = serve.Server(150 << 30, block_steps=16)
+    try:
+        rep = srv.run(reqs)
+    finally:
+        srv.close()
+    return {"trace": f"{count} requests, Poisson 20/s, N log-uniform 512-65536 (1/8 of "
+                     f"4096-524288), steps 5-250 (1/20 of 100-5000), budget 150 GB",
+            "completed": rep["completed"], "p50_latency_s": rep.get("p50_latency_s"),
+            "p99_latency_s": rep.get("p99_latency_s"), "pairs_per_s": rep["pairs_per_s"],
+            "unit_pairs": "pair-interactions/s", "wall_s": rep["wall_s"], "blocks": rep["blocks"]}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -239,6 +317,7 @@ def run_ours(args):
     sim = capi.Simulation(n, b.w, b.dt, b.eps)
     sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
     sim.load(pos0)
+    tune = None if args.no_autotune else sim.autotune()     # set-up, not timed
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize(dev)
@@ -260,10 +339,7 @@ def run_ours(args):
         torch.distributed.barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s)
     pairs = float(n) * n * args.steps * world
     value = pairs / total_s / 1e9
 
@@ -283,15 +359,14 @@ def run_ours(args):
             capi.pp_get_state(sim.ctx, hp, hv, ha)
             t_e2e += time.perf_counter() - t0
             step += 1
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e)
         e2e = {"value": float(n) * n * args.e2e_steps * world / t_e2e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 3 * n * 3 * 8,
                "api": "pp_set_state(host r,v,a) + pp_step(1) + pp_get_state(host r,v,a)"}
 
     sim.close()
+    batched = run_batched(args.batch_steps) if (args.batch_steps > 0 and world == 1) else None
+    served = run_serving(args.serve_requests) if (args.serve_requests > 0 and world == 1) else None
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -312,7 +387,10 @@ def run_ours(args):
                    "precision": "FP32 pair math, FP64 per-particle fold, FP64 r/v/a",
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "pct_fp32_peak": 100.0 * achieved / peak},
+                   "pct_fp32_peak": 100.0 * achieved / peak,
+                   "kernel": (tune or {}).get("variant_name", "default plan"),
+                   "split": (tune or {}).get("split"),
+                   "autotuned": tune is not None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
                      "note": f"{FLOP_PER_PAIR} flop per pair; peak = 2 x 128 FP32 lanes x {sms} SMs x "
@@ -321,6 +399,10 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": csum,
     }
+    if batched:
+        line["batched"] = batched
+    if served:
+        line["serving"] = served
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
