@@ -270,7 +270,7 @@ typedef struct {
 /*
  * Autotuner: time every compiled force-kernel variant that fits the
  * context's accumulation and positions modes, each with the launch planner's
- * j-split count S and with S/2 and 2S, on the context's loaded particles, and
+ * j-split count S and with S/4, S/2 and 2S, on the context's loaded particles, and
  * keep the fastest pair as the context's PP_OPT_VARIANT and PP_OPT_SPLIT.
  * Only force passes run (fields of the current positions into scratch): the
  * particle state and step counter are untouched.  Takes a few hundred force

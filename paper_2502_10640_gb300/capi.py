@@ -386,20 +386,77 @@ class Batch:
             pass
 
 
-class Simulation:
-    """Owning wrapper: one context, destroyed with the object or on close()."""
+def _tune_cache_path() -> str:
+    return os.environ.get("PP_TUNE_CACHE", os.path.join(_build.BUILD, "autotune.json"))
 
-    def __init__(self, n: int, w: float, dt: float, softening: float = 0.0, acc: int | None = None):
+
+def _tune_key(n: int, acc: int, positions: int) -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    bucket = 1 << max(0, int(n - 1).bit_length())          # next power of two
+    return f"{p.name}|{p.multi_processor_count}|n<={bucket}|acc={acc}|pos={positions}"
+
+
+class Simulation:
+    """Owning wrapper: one context, destroyed with the object or on close().
+
+    tune="cache" applies a cached autotuner choice for this device, N bucket and mode
+    (running pp_autotune and storing its choice on a miss, once particles are loaded);
+    tune="always" reruns the autotuner at every load; tune=None keeps the built-in plan.
+    """
+
+    def __init__(self, n: int, w: float, dt: float, softening: float = 0.0, acc: int | None = None,
+                 positions: int | None = None, tune: str | None = None):
         self.ctx = pp_create(n, w, dt, softening)
         self.n = n
+        self.acc = PP_ACC_FP64FOLD if acc is None else acc
+        self.positions = PP_POS_SINGLE if positions is None else positions
+        self.tune = tune
+        self.tuned = None
         if acc is not None:
             pp_set_option(self.ctx, PP_OPT_ACC, acc)
+        if positions is not None:
+            pp_set_option(self.ctx, PP_OPT_POSITIONS, positions)
+
+    def _apply_tuning(self):
+        import json
+        path = _tune_cache_path()
+        key = _tune_key(self.n, self.acc, self.positions)
+        cache = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        hit = cache.get(key) if self.tune == "cache" else None
+        names = variants()
+        if hit and hit.get("variant_name") in names:
+            pp_set_option(self.ctx, PP_OPT_VARIANT, names.index(hit["variant_name"]))
+            pp_set_option(self.ctx, PP_OPT_SPLIT, 0)
+            self.tuned = dict(hit, cached=True)
+            return
+        res = pp_autotune(self.ctx)
+        # the split count is kept only for this N; the cache stores the kernel variant
+        cache[key] = {"variant_name": res["variant_name"], "ms_per_pass": res["ms_per_pass"],
+                      "n": self.n}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = f"{path}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+        self.tuned = dict(res, cached=False)
 
     def set_option(self, key, value):
         pp_set_option(self.ctx, key, value)
 
     def load(self, pos, vel=None):
         pp_load_particles(self.ctx, pos, vel)
+        if self.tune in ("cache", "always"):
+            self._apply_tuning()
 
     def fields(self, out=None):
         return pp_compute_fields(self.ctx, out)

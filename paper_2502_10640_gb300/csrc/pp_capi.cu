@@ -125,8 +125,8 @@ const Variant *force_variant(const pp_ctx *c)
     // packed f32x2 pair math wherever there is enough work per CTA (defaults
     // from GB300 measurements; pp_autotune refines them per device and N)
     if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k512m4");
-    if (c->n >= 2048) return variant_by_name("f32x2.fold64.t128r2k128");
-    return variant_by_name("f32.fold64.t128r1k128");
+    if (c->n >= 8192) return variant_by_name("f32x2.fold64.t128r2k128");
+    return variant_by_name("f32x2.fold64.t64r1k128");
 }
 
 // Staging layout the force kernels of this context read.
@@ -761,9 +761,10 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
         c->split_override = 0;
         const Plan base = make_plan(c, KIND_FORCE32);
         const int tiles = c->npad / vs[v].tile;
-        int cand[3] = {base.nsplit, std::max(1, base.nsplit / 2), std::min(tiles, 2 * base.nsplit)};
+        int cand[4] = {base.nsplit, std::max(1, base.nsplit / 2), std::min(tiles, 2 * base.nsplit),
+                       std::max(1, base.nsplit / 4)};
         st = stage_current(c, scratch, vs[v].stage);
-        for (int k = 0; k < 3 && st == PP_OK; ++k) {
+        for (int k = 0; k < 4 && st == PP_OK; ++k) {
             bool dup = false;
             for (int q = 0; q < k; ++q) dup |= cand[q] == cand[k];
             if (dup) continue;

@@ -5,7 +5,7 @@
 // strided by T so loads coalesce) and one j-chunk of the staged source array.
 // With S > 1 chunks per i-block, each CTA writes FP64 partial sums, and the
 // CTA that finishes an i-block last (an atomic ticket decides who) adds the S
-// partials in the fixed order s = 0..S-1 and runs the epilogue.  The ticket
+// partials in an order fixed by S alone and runs the epilogue.  The ticket
 // picks only *who* sums, never the order, so results are bitwise reproducible.
 //
 // Data movement.  Staged sources are float4 (x', y', z', q') in units of a
@@ -387,7 +387,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 }
 
 // Split-path epilogue shared by all kernels: write partials, take a ticket,
-// and let the last CTA of the i-block sum the S partials in order s = 0..S-1.
+// and let the last CTA of the i-block sum the S partials (split_gather).
 // Returns true on the CTA that must finish the i-block.
 template <int T, int R>
 __device__ __forceinline__ bool split_publish(const ForceArgs &p, int ib, int split,
@@ -418,27 +418,52 @@ __device__ __forceinline__ bool split_publish(const ForceArgs &p, int ib, int sp
     return true;
 }
 
+// The finishing CTA adds the S partials of each of its targets.  For each
+// target the loads of U consecutive chunks (all three components) are issued
+// together so their L2 latencies overlap; lane u accumulates chunks u, u+U,
+// u+2U, ... and the U lanes are combined by a fixed tree.  The summation order
+// is a fixed function of S, so results stay bitwise reproducible.
 template <int T, int R>
 __device__ __forceinline__ void split_gather(const ForceArgs &p, int ib, double (&sx)[R],
                                              double (&sy)[R], double (&sz)[R], int ncomp)
 {
+    constexpr int U = 4;
     const int tid = threadIdx.x;
     const size_t stride = (size_t)p.nipad;
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < R; ++r) {
         const int i = ib * T * R + r * T + tid;
-        double ax = 0.0, ay = 0.0, az = 0.0;
-        for (int s = 0; s < p.nsplit; ++s) {
-            const double *base = p.partial + (size_t)s * ncomp * stride;
-            ax += ld_cg(base + i);
-            if (ncomp == 3) {
-                ay += ld_cg(base + stride + i);
-                az += ld_cg(base + 2 * stride + i);
+        double acc[3][U];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[c][u] = 0.0;
+        for (int s0 = 0; s0 < p.nsplit; s0 += U) {
+            double v[3][U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = s0 + u;
+                const double *base = p.partial + (size_t)s * ncomp * stride + i;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    v[c][u] = (s < p.nsplit && c < ncomp) ? ld_cg(base + c * stride) : 0.0;
             }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[c][u] += v[c][u];
         }
-        sx[r] = ax;
-        sy[r] = ay;
-        sz[r] = az;
+        double t[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t[c] = (acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3]);
+        // R is small and unrolled elsewhere; select the output slot explicitly
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (q == r) {
+                sx[q] = t[0];
+                sy[q] = t[1];
+                sz[q] = t[2];
+            }
     }
     if (tid == 0) p.tickets[ib] = 0u;
 }

@@ -61,6 +61,8 @@ const Variant kVariants[] = {
     make_f32x2<128, 4, 256, 4, 4, true>("f32x2.sfold64.t128r4k256m4"),
     make_f32x2<128, 4, 512, 3, 5, true>("f32x2.sfold64.t128r4k512m5"),
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
+    make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
+    make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
     // potential (diagnostics) and all-FP64 comparison path
     make_phi<256, 2, 256, 4>("phi32.fold64.t256r2k256"),
     make_phi<128, 1, 128, 4>("phi32.fold64.t128r1k128"),

@@ -1,0 +1,100 @@
+"""Full-size runs in the benchmark's launch plan, checked where the oracle cannot follow
+the whole run: sampled oracle forces on the GPU's own late-time state, conservation
+laws, and the closed-form expansion of a cold uniform ball."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_10640_gb300 import capi, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    capi.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def shell_scale(t, K):
+    """s(t) of a cold uniform ball: s'' = K / s^2, s(0) = 1, s'(0) = 0 (no shell crossing)."""
+    from scipy.optimize import brentq
+    tau = t * math.sqrt(2 * K)
+    f = lambda s: math.sqrt(s * (s - 1)) + math.log(math.sqrt(s) + math.sqrt(s - 1)) - tau
+    return 1.0 if tau == 0 else brentq(f, 1.0, 1e6, xtol=1e-14)
+
+
+def test_sphere_1m_expansion_and_late_forces():
+    """2^20 particles, R = 50 um, 1 nC, 100 steps of 2e-14 s (the bunch grows ~8x)."""
+    b = wl.SPHERE_1M
+    pos0 = b.positions()
+    steps = 100
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.load(pos0)
+        d0 = sim.diagnostics(with_pe=False)
+        sim.step(steps)
+        d1 = sim.diagnostics(with_pe=False)
+        p, v, a, _, _ = sim.state()
+        E = sim.fields()
+    # homologous expansion of the ball (continuum limit; sampling noise ~ 1e-3)
+    K = wl.explosion_rate(b.n, b.w, b.scale)
+    s = shell_scale(steps * b.dt, K)
+    assert s > 5
+    assert abs(d1["rms_radius"] / d0["rms_radius"] / s - 1) < 0.01
+    # total momentum stays at the FP32 summation noise level
+    pmag = math.sqrt(d1["px"] ** 2 + d1["py"] ** 2 + d1["pz"] ** 2)
+    pscale = oracle.constants()["me"] * b.w * np.linalg.norm(v, axis=1).sum()
+    assert pmag <= 1e-6 * pscale
+    # forces on the GPU's late-time state, sampled targets against all sources
+    idx = np.sort(np.unique((wl.uniform(79, 0, 512) * b.n).astype(np.int64)))
+    ref = oracle.fields_subset(p, b.w, b.eps, idx)
+    assert rel(E[idx], ref) <= 1e-5
+
+
+def test_gaussian_65536_full_run_conserves_energy_and_momentum():
+    """All 2000 steps of the benchmark bunch; energy drift and momentum at the end, and
+    sampled oracle forces on the final state."""
+    b = wl.GAUSSIAN_65536
+    pos0 = b.positions()
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.load(pos0)
+        d0 = sim.diagnostics(with_pe=True)
+        sim.step(b.steps)
+        d1 = sim.diagnostics(with_pe=True)
+        p, v, a, step, _ = sim.state()
+        E = sim.fields()
+    assert step == b.steps
+    e0 = d0["ke"] + d0["pe"]
+    e1 = d1["ke"] + d1["pe"]
+    assert d1["ke"] > 0.3 * d0["pe"]                 # a large part of the energy converted
+    assert abs(e1 / e0 - 1) < 1e-3
+    pmag = math.sqrt(d1["px"] ** 2 + d1["py"] ** 2 + d1["pz"] ** 2)
+    assert pmag <= 1e-6 * oracle.constants()["me"] * b.w * np.linalg.norm(v, axis=1).sum()
+    idx = np.sort(np.unique((wl.uniform(80, 0, 512) * b.n).astype(np.int64)))
+    assert rel(E[idx], oracle.fields_subset(p, b.w, b.eps, idx)) <= 1e-5
+
+
+def test_paper_lattice_experiment_series_matches_oracle():
+    """The 16^3 lattice of Sec. 2.1 at dt = 1e-13 s: the emittance and moment series of the
+    experiment driver against the oracle run for the first 1000 steps."""
+    from paper_2502_10640_gb300 import experiments
+    run = experiments.run_lattice(16, 1e-13, 1e-10, records=4)
+    assert run["steps"] == 1000 and len(run["series"]["emit_x"]) == 5
+    b = wl.PAPER_LATTICE
+    pos = b.positions()
+    p, v, a = pos, np.zeros_like(pos), None
+    for k in range(4):
+        p, v, a = oracle.vv_run(p, v, a, b.w, 0.0, b.dt, 250)
+        d = oracle.diagnostics(p, v, b.w)
+        for key in ("emit_x", "x_rms", "vx_rms", "rms_radius"):
+            got = run["series"][key][k + 1]
+            assert abs(got / d[key] - 1) <= 1e-5, (k, key, got, d[key])
+        assert abs(run["series"]["x_max"][k + 1] / d["x_max"] - 1) <= 1e-6
