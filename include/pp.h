@@ -107,6 +107,18 @@ pp_status pp_set_option(pp_ctx *ctx, int key, int64_t value);
 pp_status pp_load_particles(pp_ctx *ctx, const double *pos, const double *vel, int on_device);
 
 /*
+ * Per-particle weights w_i ([N] doubles, finite and > 0), replacing the common
+ * weight of pp_create, which stays the reference weight W: sources enter the
+ * sum with w_j (staged as the FP32 ratio w_j / W), and KE, PE and momentum use
+ * w_i.  w = NULL returns to equal weights.  If particles are loaded, a is
+ * recomputed for the new weights (the state stays at the same time).  Needs
+ * PP_ACC_FP64FOLD (or PP_ACC_FP64_FULL) with single positions, else
+ * PP_ERR_ARG.  The paper uses one weight for all macro-particles (Sec. 2.1);
+ * this generalises it.
+ */
+pp_status pp_set_weights(pp_ctx *ctx, const double *w, int on_device);
+
+/*
  * Field E_i (V/m) of Eq. B at every particle's current position, written as
  * [N][3] to E_out.  Does not advance or modify the state.
  */

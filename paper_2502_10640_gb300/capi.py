@@ -81,6 +81,7 @@ SIGNATURES = [
     ("pp_set_option", ctypes.c_int, [_CTX, ctypes.c_int, _I64]),
     ("pp_load_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
     ("pp_compute_fields", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
+    ("pp_set_weights", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
     ("pp_step", ctypes.c_int, [_CTX, _I64]),
     ("pp_diagnostics", ctypes.c_int, [_CTX, ctypes.POINTER(pp_diag), ctypes.c_int]),
     ("pp_get_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
@@ -224,6 +225,26 @@ def pp_load_particles(ctx, pos, vel=None) -> None:
     v, ov, k2 = _arg(vel, n, False)
     on = _same_kind(op, ov if vel is not None else None)
     _check(load().pp_load_particles(ctx, p, v, on), ctx)
+
+
+def pp_set_weights(ctx, w=None) -> None:
+    """Per-particle weights ([N] float64, host array or CUDA tensor); None = equal weights."""
+    if w is None:
+        _check(load().pp_set_weights(ctx, None, 0), ctx)
+        return
+    n = pp_get_n(ctx)
+    if _is_torch(w) and w.is_cuda:
+        import torch
+        w = w.to(torch.float64).contiguous()
+        if tuple(w.shape) != (n,):
+            raise ValueError(f"expected shape ({n},)")
+        torch.cuda.current_stream(w.device).synchronize()
+        _check(load().pp_set_weights(ctx, w.data_ptr(), 1), ctx)
+        return
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    if a.shape != (n,):
+        raise ValueError(f"expected shape ({n},)")
+    _check(load().pp_set_weights(ctx, a.ctypes.data, 0), ctx)
 
 
 def pp_compute_fields(ctx, out=None):
@@ -457,6 +478,9 @@ class Simulation:
         pp_load_particles(self.ctx, pos, vel)
         if self.tune in ("cache", "always"):
             self._apply_tuning()
+
+    def set_weights(self, w=None):
+        pp_set_weights(self.ctx, w)
 
     def fields(self, out=None):
         return pp_compute_fields(self.ctx, out)

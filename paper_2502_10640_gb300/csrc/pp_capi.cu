@@ -56,6 +56,8 @@ struct pp_ctx {
     size_t stage_bytes = 0;
     double *aos = nullptr;         // [n][3] scratch for host transfers / outputs
     double *phi = nullptr;         // [n]
+    double *wts = nullptr;         // per-particle weights [npad] (null: all equal to w)
+    float *wrel = nullptr;         // w_i / w as staged [npad]
     double *partial = nullptr;     // split partials
     size_t partial_bytes = 0;
     unsigned *tickets = nullptr;
@@ -112,11 +114,17 @@ const Variant *force_variant(const pp_ctx *c)
     if (f64_pairs(c)) return variant_by_name("f64.full.t128r2k128");
     int count = 0;
     const Variant *vs = variants(&count);
+    const int want_kind = c->wts ? KIND_FORCE32W : KIND_FORCE32;
     if (c->variant_override >= 0 && c->variant_override < count) {
         const Variant &v = vs[c->variant_override];
         const bool split = v.stage == STAGE_F32X2;
-        if (v.kind == KIND_FORCE32 && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
+        if (v.kind == want_kind && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
             return &v;
+    }
+    if (c->wts) {  // per-particle weights: packed kernels that read the weight lanes
+        if (c->n >= 32768) return variant_by_name("f32x2w.sfold64.t128r4k512m4");
+        if (c->n >= 8192) return variant_by_name("f32x2w.fold64.t128r2k128");
+        return variant_by_name("f32x2w.fold64.t64r1k128");
     }
     if (c->positions == PP_POS_SPLIT)
         return variant_by_name(c->n >= 32768 ? "f32split.fold64.t256r4k256" : "f32split.fold64.t128r2k128");
@@ -237,6 +245,7 @@ ForceArgs base_args(const pp_ctx *c, const Plan &pl, int mode, const void *src, 
     }
     a.dst = dst;
     a.out = out;
+    a.wrel = c->wrel;
     // a_i = k e^2 w / (m_e L0^2) * sum_j d'/|d'|^3   (Eq. F with Eq. E, staged units)
     a.cscale = kCoulomb * kE * kE * c->w / (kMe * c->l0 * c->l0);
     // E_i = (m_e / q_e) a_i, q_e = -e
@@ -288,7 +297,7 @@ pp_status force_pass(pp_ctx *c, int mode, const void *src, void *dst, double *ou
 pp_status stage_current(pp_ctx *c, void *dst, int kind)
 {
     PP_CUDA(launch_stage(c->r[0], c->r[1], c->r[2], (int)c->n, c->npad, dst, kind, c->cx, c->cy,
-                         c->cz, 1.0 / c->l0, c->stream));
+                         c->cz, 1.0 / c->l0, c->stream, c->wrel));
     return PP_OK;
 }
 
@@ -308,7 +317,7 @@ pp_status restage_pending(pp_ctx *c)
     if (pp_status st = pad_both(c)) return st;
     PP_CUDA(launch_stage_drift(c->r, c->v, c->a, (int)c->n, c->npad, c->stage[c->parity],
                                stage_kind(c), c->dt, c->dt * c->dt / 2.0, c->cx, c->cy, c->cz,
-                               1.0 / c->l0, c->stream));
+                               1.0 / c->l0, c->stream, c->wrel));
     PP_CUDA(cudaStreamSynchronize(c->stream));
     return PP_OK;
 }
@@ -350,7 +359,7 @@ pp_status moments(pp_ctx *c, int pass, const double *x, double out[kMomSlots])
 {
     PP_CUDA(launch_moments(pass, (int)c->n, pass == 2 ? x : c->r[0], c->r[1], c->r[2], c->v[0],
                            c->v[1], c->v[2], c->cx, c->cy, c->cz, c->mom_partials, c->mom_out,
-                           c->stream));
+                           c->stream, c->wts));
     PP_CUDA(cudaMemcpyAsync(c->mom_host, c->mom_out, kMomSlots * sizeof(double),
                             cudaMemcpyDeviceToHost, c->stream));
     PP_CUDA(cudaStreamSynchronize(c->stream));
@@ -455,6 +464,8 @@ pp_status pp_destroy(pp_ctx *c)
     cudaFree(c->stage[1]);
     cudaFree(c->aos);
     cudaFree(c->phi);
+    cudaFree(c->wts);
+    cudaFree(c->wrel);
     cudaFree(c->partial);
     cudaFree(c->tickets);
     cudaFree(c->mom_partials);
@@ -535,6 +546,8 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
         const int new_pos = key == PP_OPT_POSITIONS ? (int)value : c->positions;
         if (new_pos == PP_POS_SPLIT && new_acc == PP_ACC_KAHAN)
             return fail(PP_ERR_ARG, "split positions are implemented with the FP64 fold only");
+        if (c->wts && (new_pos == PP_POS_SPLIT || new_acc == PP_ACC_KAHAN))
+            return fail(PP_ERR_ARG, "per-particle weights need the FP64 fold and single positions");
         const int old_kind = stage_kind(c);
         c->acc = new_acc;
         c->positions = new_pos;
@@ -621,6 +634,60 @@ pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int
     c->loaded = true;
     c->step = 0;
     return PP_OK;
+}
+
+pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
+{
+    if (pp_status s = check_ctx(c)) return s;
+    PP_CUDA(cudaSetDevice(c->device));
+    if (c->acc == PP_ACC_KAHAN || c->positions == PP_POS_SPLIT)
+        return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL "
+                                "with single positions");
+    const int old_kind = stage_kind(c);
+    if (!w) {
+        cudaFree(c->wts);
+        cudaFree(c->wrel);
+        c->wts = nullptr;
+        c->wrel = nullptr;
+    } else {
+        if (!c->wts) {
+            if (cudaMalloc(&c->wts, (size_t)c->npad * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&c->wrel, (size_t)c->npad * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(c->wts);
+                cudaFree(c->wrel);
+                c->wts = nullptr;
+                c->wrel = nullptr;
+                return fail(PP_ERR_NOMEM, "cannot allocate the weight arrays");
+            }
+        }
+        const size_t bytes = (size_t)c->n * sizeof(double);
+        PP_CUDA(cudaMemcpyAsync(c->wts, w, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                             : cudaMemcpyHostToDevice, c->stream));
+        int bad = 0;
+        PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
+        PP_CUDA(launch_weights(c->wts, (int)c->n, c->w, c->wrel, c->err + 1, c->stream));
+        PP_CUDA(cudaMemcpyAsync(&bad, c->err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PP_CUDA(cudaStreamSynchronize(c->stream));
+        if (bad) {
+            PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
+            cudaFree(c->wts);
+            cudaFree(c->wrel);
+            c->wts = nullptr;
+            c->wrel = nullptr;
+            return fail(PP_ERR_ARG, "weights must be finite and > 0");
+        }
+    }
+    drop_graphs(c);
+    if (!c->loaded) return PP_OK;
+    // the acceleration belongs to the weights: recompute a(r) and restage r_{n+1}
+    (void)old_kind;
+    pp_status st = pad_both(c);
+    if (st == PP_OK) st = stage_current(c, c->stage[c->parity ^ 1], stage_kind(c));
+    if (st == PP_OK)
+        st = force_pass(c, MODE_INIT, c->stage[c->parity ^ 1], c->stage[c->parity], nullptr);
+    if (st == PP_OK) st = check_device_errors(c, true);
+    return st;
 }
 
 pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const double *acc,
@@ -754,12 +821,12 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
     pp_status st = PP_OK;
     for (int v = 0; v < count && st == PP_OK; ++v) {
         const bool split_layout = vs[v].stage == STAGE_F32X2;
-        if (vs[v].kind != KIND_FORCE32 || vs[v].acc != c->acc ||
+        if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
             split_layout != (c->positions == PP_POS_SPLIT))
             continue;
         c->variant_override = v;
         c->split_override = 0;
-        const Plan base = make_plan(c, KIND_FORCE32);
+        const Plan base = make_plan(c, vs[v].kind);
         const int tiles = c->npad / vs[v].tile;
         int cand[4] = {base.nsplit, std::max(1, base.nsplit / 2), std::min(tiles, 2 * base.nsplit),
                        std::max(1, base.nsplit / 4)};
@@ -840,7 +907,8 @@ pp_status pp_diagnostics(pp_ctx *c, pp_diag *d, int with_pe)
     c->cy = scy;
     c->cz = scz;
     if (st != PP_OK) return st;
-    const double mw = kMe * c->w;
+    // with per-particle weights the moment sums already carry w_i
+    const double mw = c->wts ? kMe : kMe * c->w;
     d->t = (double)c->step * c->dt;
     d->step = c->step;
     d->rms_radius = std::sqrt(m1[0] / n);
@@ -871,7 +939,8 @@ pp_status pp_diagnostics(pp_ctx *c, pp_diag *d, int with_pe)
         double mp[kMomSlots];
         st = moments(c, 2, c->phi, mp);
         if (st != PP_OK) return st;
-        d->pe = 0.5 * kCoulomb * kE * kE * c->w * c->w / c->l0 * mp[0];
+        // sum_i w_i phi'_i (weights) or sum_i phi'_i (equal weights, times w)
+        d->pe = 0.5 * kCoulomb * kE * kE * c->w / c->l0 * mp[0] * (c->wts ? 1.0 : c->w);
     }
     return PP_OK;
 }

@@ -57,6 +57,7 @@ struct ForceArgs {
     double *a[3];
     void *dst;              // staging written by the epilogue (float4 or double4)
     double *out;            // fields [n][3] (MODE_FIELDS) or phi [n] (MODE_PHI)
+    const float *wrel;      // per-particle weight / reference weight, or null (all 1)
     double cscale;          // a = cscale * sum
     double escale;          // E = escale * sum
     double dt, half_dt, half_dt2;
@@ -88,6 +89,8 @@ __device__ __forceinline__ double kick(double v, double a_old, double a_new, dou
 //               32 bytes of pair k = (2k, 2k+1) hold x_2k x_2k+1 y_2k y_2k+1
 //               z_2k z_2k+1 w_2k w_2k+1 (same 16 bytes per source as STAGE_F32).
 // p' = (r - centre) / L0 with L0 a power of two, so the scaling is exact.
+// The weight slot carries w_j / W (W the context's reference weight; 1 for
+// equal weights); kernels that assume equal weights do not read it.
 // Padding entries (n <= i < npad) sit at 1e18 with weight 0.
 enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2, STAGE_F32I = 3 };
 
@@ -109,20 +112,20 @@ __device__ __forceinline__ double staged_coord(double x, double c, double inv_l0
 template <int KIND>
 __device__ __forceinline__ void store_staged(void *dst, int npad, int i, double x, double y,
                                              double z, double cx, double cy, double cz,
-                                             double inv_l0)
+                                             double inv_l0, float qw = 1.0f)
 {
     const double px = staged_coord(x, cx, inv_l0);
     const double py = staged_coord(y, cy, inv_l0);
     const double pz = staged_coord(z, cz, inv_l0);
     if (KIND == STAGE_F64) {
-        static_cast<double4 *>(dst)[i] = make_double4(px, py, pz, 1.0);
+        static_cast<double4 *>(dst)[i] = make_double4(px, py, pz, (double)qw);
     } else if (KIND == STAGE_F32I) {
         store_interleaved(dst, i, __double2float_rn(px), __double2float_rn(py),
-                          __double2float_rn(pz), 1.0f);
+                          __double2float_rn(pz), qw);
     } else {
         const float hx = __double2float_rn(px), hy = __double2float_rn(py),
                     hz = __double2float_rn(pz);
-        static_cast<float4 *>(dst)[i] = make_float4(hx, hy, hz, 1.0f);
+        static_cast<float4 *>(dst)[i] = make_float4(hx, hy, hz, qw);
         if (KIND == STAGE_F32X2)
             static_cast<float4 *>(dst)[(size_t)npad + i] =
                 make_float4(__double2float_rn(px - (double)hx), __double2float_rn(py - (double)hy),
@@ -180,7 +183,8 @@ __device__ __forceinline__ void finish_particle(const ForceArgs &p, int i, doubl
             rn[c] = drift(p.r[c][i], p.v[c][i], an[c], p.dt, p.half_dt2);
         }
     }
-    store_staged<KIND>(p.dst, p.npad, i, rn[0], rn[1], rn[2], p.cx, p.cy, p.cz, p.inv_l0);
+    store_staged<KIND>(p.dst, p.npad, i, rn[0], rn[1], rn[2], p.cx, p.cy, p.cz, p.inv_l0,
+                       p.wrel ? p.wrel[i] : 1.0f);
 }
 
 // Shared-memory ring + barriers of one CTA.  With TWO, every stage holds a
@@ -717,7 +721,7 @@ __global__ void __launch_bounds__(T) force_f64_kernel(const ForceArgs p)
                     const double s = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
                     if (s > 0.0) {
                         const double inv = rsqrt(s);
-                        const double inv3 = inv * inv * inv;
+                        const double inv3 = q.w * inv * inv * inv;  // source weight ratio
                         ax[r] = fma(inv3, dx, ax[r]);
                         ay[r] = fma(inv3, dy, ay[r]);
                         az[r] = fma(inv3, dz, az[r]);
@@ -788,7 +792,7 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
 
 // Scalar loop over an interleaved tile for one target: pairs with s == 0 add
 // nothing (the fallback when a packed tile sum is not finite).
-template <int TILE>
+template <int TILE, bool WEIGHTED = false>
 __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ tile, float x,
                                                       float y, float z, float eps2)
 {
@@ -801,7 +805,7 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
         const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         if (s > 0.f) {
             const float inv = rsqrt_sfu(s);
-            const float inv3 = inv * inv * inv;
+            const float inv3 = WEIGHTED ? inv * inv * inv * q[6] : inv * inv * inv;
             ax = fmaf(inv3, dx, ax);
             ay = fmaf(inv3, dy, ay);
             az = fmaf(inv3, dz, az);
@@ -813,7 +817,10 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
 // SMEM_ACC keeps the FP64 fold accumulators in shared memory (BI x 3 doubles
 // per CTA) instead of registers, trading a shared load/store per fold for
 // fewer registers and so more resident warps.
-template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false>
+// WEIGHTED multiplies each pair term by the source's weight ratio w_j / W
+// (taken from the staged weight lanes): one more f32x2 multiply per two pairs.
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
+          bool WEIGHTED = false>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
     constexpr int BI = T * R;
@@ -881,6 +888,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                 const float4 a = tile[2 * k];       // x0 x1 y0 y1
                 const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1
                 const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
+                const f2_t WJ = f2_pack(b.z, b.w);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const f2_t DX = f2_sub(X[r], XJ);
@@ -890,7 +898,8 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                     float s0, s1;
                     f2_unpack(S, s0, s1);
                     const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
-                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
+                    const f2_t INV3 = WEIGHTED ? f2_mul(f2_mul(f2_mul(INV, INV), INV), WJ)
+                                               : f2_mul(f2_mul(INV, INV), INV);
                     AX[r] = f2_fma(INV3, DX, AX[r]);
                     AY[r] = f2_fma(INV3, DY, AY[r]);
                     AZ[r] = f2_fma(INV3, DZ, AZ[r]);
@@ -908,7 +917,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                     f2_unpack(X[r], xs, dummy);
                     f2_unpack(Y[r], ys, dummy);
                     f2_unpack(Z[r], zs, dummy);
-                    const float3 f = tile_safe1_interleaved<TILE>(
+                    const float3 f = tile_safe1_interleaved<TILE, WEIGHTED>(
                         reinterpret_cast<const float *>(tile), xs, ys, zs, p.eps2f);
                     fx = f.x;
                     fy = f.y;

@@ -20,7 +20,7 @@ constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);  // 1/(4 pi eps0), Eq. A
 // Staged arrays are padded to a multiple of this many entries.
 constexpr int kPad = 1024;
 
-enum Kind : int { KIND_FORCE32 = 0, KIND_PHI32 = 1, KIND_FORCE64 = 2 };
+enum Kind : int { KIND_FORCE32 = 0, KIND_PHI32 = 1, KIND_FORCE64 = 2, KIND_FORCE32W = 3 };
 
 struct Variant {
     const char *name;
@@ -49,9 +49,14 @@ cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z,
                               double *out, cudaStream_t s);
 // Stage FP64 positions into float4 (or double4) sources; entries n..npad-1
 // become padding (far away, weight 0).
+// wrel: per-particle weight ratios written into the weight slot (null: 1).
 cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
                          void *dst, int stage_kind, double cx, double cy, double cz, double inv_l0,
-                         cudaStream_t s);
+                         cudaStream_t s, const float *wrel = nullptr);
+
+// Weight ratios wrel[i] = (float)(w[i] / w_ref); sets *bad if a weight is not finite or <= 0.
+cudaError_t launch_weights(const double *w, int n, double w_ref, float *wrel, int *bad,
+                           cudaStream_t s);
 
 // Write the padding entries n..npad-1 of a staging buffer (far away, weight 0).
 cudaError_t launch_fill_padding(void *dst, int n, int npad, int stage_kind, cudaStream_t s);
@@ -60,18 +65,20 @@ cudaError_t launch_fill_padding(void *dst, int n, int npad, int stage_kind, cuda
 // epilogue stages them (used after a state is restored).
 cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
                                int npad, void *dst, int stage_kind, double dt, double half_dt2,
-                               double cx, double cy, double cz, double inv_l0, cudaStream_t s);
+                               double cx, double cy, double cz, double inv_l0, cudaStream_t s,
+                               const float *wrel = nullptr);
 
 // Moments over n particles in a fixed reduction order.
 //  pass 0: sums of x, y, z                                     -> out[0..2]
-//  pass 1: sum |r-c|^2, sum |v|^2, sum vx, vy, vz, sum x^2,
+//  pass 1: sum |r-c|^2, sum w|v|^2, sum w vx, w vy, w vz, sum x^2,
 //          sum vx^2, sum x vx (out[0..7]); max x, max vx (out[10], out[11])
-//  pass 2: sum of the values in x (one array)                  -> out[0]
+//  pass 2: sum of w times the values in x (one array)          -> out[0]
+// wts: per-particle weights, or null for weight 1.
 constexpr int kMomSlots = 12;
 constexpr int kMomBlocks = 240;
 cudaError_t launch_moments(int pass, int n, const double *x, const double *y, const double *z,
                            const double *vx, const double *vy, const double *vz, double cx,
                            double cy, double cz, double *block_partials, double *out,
-                           cudaStream_t s);
+                           cudaStream_t s, const double *wts = nullptr);
 
 }  // namespace ppk

@@ -18,12 +18,13 @@ Variant make_f32(const char *name)
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1)};
 }
 
-template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false>
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false, bool WEIGHTED = false>
 Variant make_f32x2(const char *name)
 {
-    return Variant{name, KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R, TILE, STAGES,
+    return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R,
+                   TILE, STAGES,
                    reinterpret_cast<const void *>(
-                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC>),
+                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED>),
                    (size_t)STAGES * TILE * sizeof(float4) +
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
 }
@@ -63,6 +64,10 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
+    // per-particle weights (sources scaled by w_j / W)
+    make_f32x2<128, 4, 512, 3, 4, true, true>("f32x2w.sfold64.t128r4k512m4"),
+    make_f32x2<128, 2, 128, 4, 4, false, true>("f32x2w.fold64.t128r2k128"),
+    make_f32x2<64, 1, 128, 4, 8, false, true>("f32x2w.fold64.t64r1k128"),
     // potential (diagnostics) and all-FP64 comparison path
     make_phi<256, 2, 256, 4>("phi32.fold64.t256r2k256"),
     make_phi<128, 1, 128, 4>("phi32.fold64.t128r1k128"),
@@ -121,10 +126,12 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ x, const double *__
 template <int KIND>
 __global__ void stage_kernel(const double *__restrict__ x, const double *__restrict__ y,
                              const double *__restrict__ z, int n, int npad, void *dst, double cx,
-                             double cy, double cz, double inv_l0)
+                             double cy, double cz, double inv_l0, const float *__restrict__ wrel)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-        if (i < n) store_staged<KIND>(dst, npad, i, x[i], y[i], z[i], cx, cy, cz, inv_l0);
+        if (i < n)
+            store_staged<KIND>(dst, npad, i, x[i], y[i], z[i], cx, cy, cz, inv_l0,
+                               wrel ? wrel[i] : 1.0f);
         else store_padding<KIND>(dst, npad, i);
     }
 }
@@ -136,16 +143,27 @@ __global__ void stage_drift_kernel(const double *__restrict__ rx, const double *
                                    const double *__restrict__ ax, const double *__restrict__ ay,
                                    const double *__restrict__ az, int n, int npad, void *dst,
                                    double dt, double half_dt2, double cx, double cy, double cz,
-                                   double inv_l0)
+                                   double inv_l0, const float *__restrict__ wrel)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
         if (i < n) {
             store_staged<KIND>(dst, npad, i, drift(rx[i], vx[i], ax[i], dt, half_dt2),
                                drift(ry[i], vy[i], ay[i], dt, half_dt2),
-                               drift(rz[i], vz[i], az[i], dt, half_dt2), cx, cy, cz, inv_l0);
+                               drift(rz[i], vz[i], az[i], dt, half_dt2), cx, cy, cz, inv_l0,
+                               wrel ? wrel[i] : 1.0f);
         } else {
             store_padding<KIND>(dst, npad, i);
         }
+    }
+}
+
+__global__ void weights_kernel(const double *__restrict__ w, int n, double inv_ref, float *wrel,
+                               int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x = w[i];
+        if (!(isfinite(x) && x > 0.0)) atomicOr(bad, 1);
+        wrel[i] = __double2float_rn(x * inv_ref);
     }
 }
 
@@ -168,7 +186,7 @@ __global__ void __launch_bounds__(kMomThreads)
     moments_kernel(int pass, int n, const double *__restrict__ x, const double *__restrict__ y,
                    const double *__restrict__ z, const double *__restrict__ vx,
                    const double *__restrict__ vy, const double *__restrict__ vz, double cx,
-                   double cy, double cz, double *partials)
+                   double cy, double cz, double *partials, const double *__restrict__ wts)
 {
     __shared__ double sh[kMomSlots * kMomThreads];
     double acc[kMomSlots];
@@ -185,18 +203,19 @@ __global__ void __launch_bounds__(kMomThreads)
             acc[2] += z[i];
         } else if (pass == 1) {
             const double dx = x[i] - cx, dy = y[i] - cy, dz = z[i] - cz;
+            const double wi = wts ? wts[i] : 1.0;
             acc[0] += dx * dx + dy * dy + dz * dz;
-            acc[1] += vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
-            acc[2] += vx[i];
-            acc[3] += vy[i];
-            acc[4] += vz[i];
+            acc[1] += wi * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+            acc[2] += wi * vx[i];
+            acc[3] += wi * vy[i];
+            acc[4] += wi * vz[i];
             acc[5] += x[i] * x[i];
             acc[6] += vx[i] * vx[i];
             acc[7] += x[i] * vx[i];
             acc[10] = fmax(acc[10], x[i]);
             acc[11] = fmax(acc[11], vx[i]);
         } else {
-            acc[0] += x[i];
+            acc[0] += wts ? wts[i] * x[i] : x[i];
         }
     }
     for (int k = 0; k < kMomSlots; ++k) block_sum(sh, k, acc[k]);
@@ -254,17 +273,24 @@ cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z,
 
 cudaError_t launch_stage(const double *x, const double *y, const double *z, int n, int npad,
                          void *dst, int kind, double cx, double cy, double cz, double inv_l0,
-                         cudaStream_t s)
+                         cudaStream_t s, const float *wrel)
 {
     const int g = grid_for(npad, 256);
     if (kind == STAGE_F32I)
-        stage_kernel<STAGE_F32I><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+        stage_kernel<STAGE_F32I><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
     else if (kind == STAGE_F32)
-        stage_kernel<STAGE_F32><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+        stage_kernel<STAGE_F32><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
     else if (kind == STAGE_F32X2)
-        stage_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+        stage_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
     else
-        stage_kernel<STAGE_F64><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0);
+        stage_kernel<STAGE_F64><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(const double *w, int n, double w_ref, float *wrel, int *bad,
+                           cudaStream_t s)
+{
+    weights_kernel<<<grid_for(n, 256), 256, 0, s>>>(w, n, 1.0 / w_ref, wrel, bad);
     return cudaGetLastError();
 }
 
@@ -281,11 +307,12 @@ cudaError_t launch_fill_padding(void *dst, int n, int npad, int kind, cudaStream
 
 cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *const a[3], int n,
                                int npad, void *dst, int kind, double dt, double half_dt2,
-                               double cx, double cy, double cz, double inv_l0, cudaStream_t s)
+                               double cx, double cy, double cz, double inv_l0, cudaStream_t s,
+                               const float *wrel)
 {
     const int g = grid_for(npad, 256);
 #define PP_SD_ARGS r[0], r[1], r[2], v[0], v[1], v[2], a[0], a[1], a[2], n, npad, dst, dt, half_dt2, \
-                   cx, cy, cz, inv_l0
+                   cx, cy, cz, inv_l0, wrel
     if (kind == STAGE_F32I) stage_drift_kernel<STAGE_F32I><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else if (kind == STAGE_F32) stage_drift_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else if (kind == STAGE_F32X2) stage_drift_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_SD_ARGS);
@@ -297,10 +324,10 @@ cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *c
 cudaError_t launch_moments(int pass, int n, const double *x, const double *y, const double *z,
                            const double *vx, const double *vy, const double *vz, double cx,
                            double cy, double cz, double *block_partials, double *out,
-                           cudaStream_t s)
+                           cudaStream_t s, const double *wts)
 {
     moments_kernel<<<kMomBlocks, kMomThreads, 0, s>>>(pass, n, x, y, z, vx, vy, vz, cx, cy, cz,
-                                                      block_partials);
+                                                      block_partials, wts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     moments_finish_kernel<<<1, 32, 0, s>>>(block_partials, kMomBlocks, out);
