@@ -7,7 +7,7 @@
 // so a bunch's results are bitwise the same alone or in any mix.  CTAs pull
 // items from a global queue (one atomic per item); which CTA computes an item
 // does not change its arithmetic, and the S partial sums of a target block are
-// added by the last arriving CTA in the fixed order s = 0..S-1.
+// added by the last arriving CTA in an order fixed by S.
 #pragma once
 
 #include "pp_force.cuh"
@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(T, MINB)
                         f2_unpack(Y[r], ys, dummy);
                         f2_unpack(Z[r], zs, dummy);
                         const float3 f = tile_safe1_interleaved<TILE>(
-                            reinterpret_cast<const float *>(tile), xs, ys, zs, p.eps2f);
+                            reinterpret_cast<const float *>(tile), nullptr, xs, ys, zs, 0.f, 0.f,
+                            0.f, p.eps2f);
                         fx = f.x;
                         fy = f.y;
                         fz = f.z;

@@ -117,7 +117,7 @@ const Variant *force_variant(const pp_ctx *c)
     const int want_kind = c->wts ? KIND_FORCE32W : KIND_FORCE32;
     if (c->variant_override >= 0 && c->variant_override < count) {
         const Variant &v = vs[c->variant_override];
-        const bool split = v.stage == STAGE_F32X2;
+        const bool split = v.stage == STAGE_F32X2 || v.stage == STAGE_F32IX2;
         if (v.kind == want_kind && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
             return &v;
     }
@@ -126,8 +126,11 @@ const Variant *force_variant(const pp_ctx *c)
         if (c->n >= 8192) return variant_by_name("f32x2w.fold64.t128r2k128");
         return variant_by_name("f32x2w.fold64.t64r1k128");
     }
-    if (c->positions == PP_POS_SPLIT)
-        return variant_by_name(c->n >= 32768 ? "f32split.fold64.t256r4k256" : "f32split.fold64.t128r2k128");
+    if (c->positions == PP_POS_SPLIT) {
+        if (c->n >= 32768) return variant_by_name("f32x2split.sfold64.t128r2k512m4");
+        if (c->n >= 8192) return variant_by_name("f32x2split.sfold64.t128r4k256m4");
+        return variant_by_name("f32x2split.fold64.t64r1k128");
+    }
     if (c->acc == PP_ACC_KAHAN)
         return variant_by_name(c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128");
     // packed f32x2 pair math wherever there is enough work per CTA (defaults
@@ -820,7 +823,7 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
     double best_ms = 1e300;
     pp_status st = PP_OK;
     for (int v = 0; v < count && st == PP_OK; ++v) {
-        const bool split_layout = vs[v].stage == STAGE_F32X2;
+        const bool split_layout = vs[v].stage == STAGE_F32X2 || vs[v].stage == STAGE_F32IX2;
         if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
             split_layout != (c->positions == PP_POS_SPLIT))
             continue;

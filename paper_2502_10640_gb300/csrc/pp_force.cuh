@@ -88,11 +88,14 @@ __device__ __forceinline__ double kick(double v, double a_old, double a_new, dou
 //  STAGE_F32I:  sources interleaved by pairs for packed f32x2 arithmetic: the
 //               32 bytes of pair k = (2k, 2k+1) hold x_2k x_2k+1 y_2k y_2k+1
 //               z_2k z_2k+1 w_2k w_2k+1 (same 16 bytes per source as STAGE_F32).
+//  STAGE_F32IX2: the hi parts in the interleaved layout, followed (at float
+//               offset 4 npad) by the lo parts in the same layout.
 // p' = (r - centre) / L0 with L0 a power of two, so the scaling is exact.
 // The weight slot carries w_j / W (W the context's reference weight; 1 for
 // equal weights); kernels that assume equal weights do not read it.
 // Padding entries (n <= i < npad) sit at 1e18 with weight 0.
-enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2, STAGE_F32I = 3 };
+enum StageKind : int { STAGE_F32 = 0, STAGE_F32X2 = 1, STAGE_F64 = 2, STAGE_F32I = 3,
+                       STAGE_F32IX2 = 4 };
 
 __device__ __forceinline__ void store_interleaved(void *dst, int i, float x, float y, float z,
                                                   float w)
@@ -119,9 +122,14 @@ __device__ __forceinline__ void store_staged(void *dst, int npad, int i, double 
     const double pz = staged_coord(z, cz, inv_l0);
     if (KIND == STAGE_F64) {
         static_cast<double4 *>(dst)[i] = make_double4(px, py, pz, (double)qw);
-    } else if (KIND == STAGE_F32I) {
-        store_interleaved(dst, i, __double2float_rn(px), __double2float_rn(py),
-                          __double2float_rn(pz), qw);
+    } else if (KIND == STAGE_F32I || KIND == STAGE_F32IX2) {
+        const float hx = __double2float_rn(px), hy = __double2float_rn(py),
+                    hz = __double2float_rn(pz);
+        store_interleaved(dst, i, hx, hy, hz, qw);
+        if (KIND == STAGE_F32IX2)
+            store_interleaved(static_cast<float *>(dst) + 4 * (size_t)npad, i,
+                              __double2float_rn(px - (double)hx), __double2float_rn(py - (double)hy),
+                              __double2float_rn(pz - (double)hz), 0.0f);
     } else {
         const float hx = __double2float_rn(px), hy = __double2float_rn(py),
                     hz = __double2float_rn(pz);
@@ -138,8 +146,10 @@ __device__ __forceinline__ void store_padding(void *dst, int npad, int i)
 {
     if (KIND == STAGE_F64) {
         static_cast<double4 *>(dst)[i] = make_double4(1e18, 1e18, 1e18, 0.0);
-    } else if (KIND == STAGE_F32I) {
+    } else if (KIND == STAGE_F32I || KIND == STAGE_F32IX2) {
         store_interleaved(dst, i, 1e18f, 1e18f, 1e18f, 0.f);
+        if (KIND == STAGE_F32IX2)
+            store_interleaved(static_cast<float *>(dst) + 4 * (size_t)npad, i, 0.f, 0.f, 0.f, 0.f);
     } else {
         static_cast<float4 *>(dst)[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
         if (KIND == STAGE_F32X2)
@@ -776,6 +786,13 @@ __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
     return d;
 }
 
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
 {
     f2_t d;
@@ -792,16 +809,24 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
 
 // Scalar loop over an interleaved tile for one target: pairs with s == 0 add
 // nothing (the fallback when a packed tile sum is not finite).
-template <int TILE, bool WEIGHTED = false>
-__device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ tile, float x,
-                                                      float y, float z, float eps2)
+template <int TILE, bool WEIGHTED = false, bool SPLITPOS = false>
+__device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ tile,
+                                                      const float *__restrict__ tlo, float x,
+                                                      float y, float z, float xl, float yl,
+                                                      float zl, float eps2)
 {
     float ax = 0.f, ay = 0.f, az = 0.f;
     for (int j = 0; j < TILE; ++j) {
         const float *q = tile + 8 * (j >> 1) + (j & 1);
-        const float dx = x - q[0];
-        const float dy = y - q[2];
-        const float dz = z - q[4];
+        float dx = x - q[0];
+        float dy = y - q[2];
+        float dz = z - q[4];
+        if (SPLITPOS) {
+            const float *ql = tlo + 8 * (j >> 1) + (j & 1);
+            dx = dx + (xl - ql[0]);
+            dy = dy + (yl - ql[2]);
+            dz = dz + (zl - ql[4]);
+        }
         const float s = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         if (s > 0.f) {
             const float inv = rsqrt_sfu(s);
@@ -819,8 +844,11 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
 // fewer registers and so more resident warps.
 // WEIGHTED multiplies each pair term by the source's weight ratio w_j / W
 // (taken from the staged weight lanes): one more f32x2 multiply per two pairs.
+// SPLITPOS reads hi/lo staged sources (STAGE_F32IX2) and forms each
+// separation as (hi_i - hi_j) + (lo_i - lo_j): three f32x2 operations per
+// component instead of one.
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false>
+          bool WEIGHTED = false, bool SPLITPOS = false>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
     constexpr int BI = T * R;
@@ -837,10 +865,12 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     const int j1 = min(j0 + p.jchunk, p.npad);
     const int ntiles = (j1 - j0) / TILE;
 
-    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), nullptr, bar_full,
-                                  bar_empty};
-    // FP64 accumulators in shared memory follow the tile ring: [3][BI]
-    double *sacc = reinterpret_cast<double *>(smem_raw + (size_t)STAGES * TILE * sizeof(float4));
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw);
+    Ring<float4, TILE, STAGES, SPLITPOS> rg{ring, SPLITPOS ? ring + STAGES * TILE : nullptr,
+                                            bar_full, bar_empty};
+    // FP64 accumulators in shared memory follow the tile ring(s): [3][BI]
+    double *sacc = reinterpret_cast<double *>(
+        smem_raw + (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1));
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
@@ -857,20 +887,30 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     __syncthreads();
 
     const float *srcf = static_cast<const float *>(p.src);
-    f2_t X[R], Y[R], Z[R];
+    f2_t X[R], Y[R], Z[R], XL[R], YL[R], ZL[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r * T + tid;
         float x = -1e18f, y = -1e18f, z = -1e18f;  // targets past n: far from everything
+        float xl = 0.f, yl = 0.f, zl = 0.f;
         if (i < p.n) {
             const float *q = srcf + 8 * (size_t)(i >> 1) + (i & 1);
             x = q[0];
             y = q[2];
             z = q[4];
+            if (SPLITPOS) {
+                const float *ql = q + 4 * (size_t)p.npad;
+                xl = ql[0];
+                yl = ql[2];
+                zl = ql[4];
+            }
         }
         X[r] = f2_pack(x, x);
         Y[r] = f2_pack(y, y);
         Z[r] = f2_pack(z, z);
+        XL[r] = f2_pack(xl, xl);
+        YL[r] = f2_pack(yl, yl);
+        ZL[r] = f2_pack(zl, zl);
     }
     double ax64[R], ay64[R], az64[R];
 #pragma unroll
@@ -878,8 +918,8 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     const f2_t EPS2 = f2_pack(p.eps2f, p.eps2f);
 
     int issued = 0, seen = 0;
-    const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
-        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int) {
+    const bool ok = run_tiles<float4, T, TILE, STAGES, SPLITPOS>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int) {
             f2_t AX[R], AY[R], AZ[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
@@ -889,11 +929,24 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                 const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1
                 const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
                 const f2_t WJ = f2_pack(b.z, b.w);
+                f2_t XJL = 0ull, YJL = 0ull, ZJL = 0ull;
+                if (SPLITPOS) {
+                    const float4 al = tlo[2 * k];
+                    const float4 bl = tlo[2 * k + 1];
+                    XJL = f2_pack(al.x, al.y);
+                    YJL = f2_pack(al.z, al.w);
+                    ZJL = f2_pack(bl.x, bl.y);
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const f2_t DX = f2_sub(X[r], XJ);
-                    const f2_t DY = f2_sub(Y[r], YJ);
-                    const f2_t DZ = f2_sub(Z[r], ZJ);
+                    f2_t DX = f2_sub(X[r], XJ);
+                    f2_t DY = f2_sub(Y[r], YJ);
+                    f2_t DZ = f2_sub(Z[r], ZJ);
+                    if (SPLITPOS) {
+                        DX = f2_add(DX, f2_sub(XL[r], XJL));
+                        DY = f2_add(DY, f2_sub(YL[r], YJL));
+                        DZ = f2_add(DZ, f2_sub(ZL[r], ZJL));
+                    }
                     const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
                     float s0, s1;
                     f2_unpack(S, s0, s1);
@@ -913,12 +966,16 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                 f2_unpack(AZ[r], z0, z1);
                 float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
                 if (!isfinite(fx + fy + fz)) {
-                    float xs, ys, zs, dummy;
+                    float xs, ys, zs, xl, yl, zl, dummy;
                     f2_unpack(X[r], xs, dummy);
                     f2_unpack(Y[r], ys, dummy);
                     f2_unpack(Z[r], zs, dummy);
-                    const float3 f = tile_safe1_interleaved<TILE, WEIGHTED>(
-                        reinterpret_cast<const float *>(tile), xs, ys, zs, p.eps2f);
+                    f2_unpack(XL[r], xl, dummy);
+                    f2_unpack(YL[r], yl, dummy);
+                    f2_unpack(ZL[r], zl, dummy);
+                    const float3 f = tile_safe1_interleaved<TILE, WEIGHTED, SPLITPOS>(
+                        reinterpret_cast<const float *>(tile), reinterpret_cast<const float *>(tlo),
+                        xs, ys, zs, xl, yl, zl, p.eps2f);
                     fx = f.x;
                     fy = f.y;
                     fz = f.z;
@@ -957,7 +1014,8 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        finish_particle<STAGE_F32I>(p, i0 + r * T + tid, ax64[r], ay64[r], az64[r]);
+        finish_particle<SPLITPOS ? STAGE_F32IX2 : STAGE_F32I>(p, i0 + r * T + tid, ax64[r],
+                                                              ay64[r], az64[r]);
 }
 
 }  // namespace ppk

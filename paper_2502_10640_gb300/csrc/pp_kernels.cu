@@ -18,14 +18,15 @@ Variant make_f32(const char *name)
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1)};
 }
 
-template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false, bool WEIGHTED = false>
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
+          bool WEIGHTED = false, bool SPLITPOS = false>
 Variant make_f32x2(const char *name)
 {
-    return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R,
-                   TILE, STAGES,
+    return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, ACC_FP64FOLD,
+                   SPLITPOS ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
-                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED>),
-                   (size_t)STAGES * TILE * sizeof(float4) +
+                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS>),
+                   (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1) +
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
 }
 
@@ -64,6 +65,10 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
+    // packed pair math on hi/lo split positions
+    make_f32x2<128, 2, 512, 3, 4, true, false, true>("f32x2split.sfold64.t128r2k512m4"),
+    make_f32x2<128, 4, 256, 3, 4, true, false, true>("f32x2split.sfold64.t128r4k256m4"),
+    make_f32x2<64, 1, 128, 4, 8, false, false, true>("f32x2split.fold64.t64r1k128"),
     // per-particle weights (sources scaled by w_j / W)
     make_f32x2<128, 4, 512, 3, 4, true, true>("f32x2w.sfold64.t128r4k512m4"),
     make_f32x2<128, 2, 128, 4, 4, false, true>("f32x2w.fold64.t128r2k128"),
@@ -276,7 +281,9 @@ cudaError_t launch_stage(const double *x, const double *y, const double *z, int 
                          cudaStream_t s, const float *wrel)
 {
     const int g = grid_for(npad, 256);
-    if (kind == STAGE_F32I)
+    if (kind == STAGE_F32IX2)
+        stage_kernel<STAGE_F32IX2><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
+    else if (kind == STAGE_F32I)
         stage_kernel<STAGE_F32I><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
     else if (kind == STAGE_F32)
         stage_kernel<STAGE_F32><<<g, 256, 0, s>>>(x, y, z, n, npad, dst, cx, cy, cz, inv_l0, wrel);
@@ -298,7 +305,8 @@ cudaError_t launch_fill_padding(void *dst, int n, int npad, int kind, cudaStream
 {
     if (npad <= n) return cudaSuccess;
     const int g = grid_for(npad - n, 256);
-    if (kind == STAGE_F32I) fill_padding_kernel<STAGE_F32I><<<g, 256, 0, s>>>(dst, n, npad);
+    if (kind == STAGE_F32IX2) fill_padding_kernel<STAGE_F32IX2><<<g, 256, 0, s>>>(dst, n, npad);
+    else if (kind == STAGE_F32I) fill_padding_kernel<STAGE_F32I><<<g, 256, 0, s>>>(dst, n, npad);
     else if (kind == STAGE_F32) fill_padding_kernel<STAGE_F32><<<g, 256, 0, s>>>(dst, n, npad);
     else if (kind == STAGE_F32X2) fill_padding_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(dst, n, npad);
     else fill_padding_kernel<STAGE_F64><<<g, 256, 0, s>>>(dst, n, npad);
@@ -313,7 +321,8 @@ cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *c
     const int g = grid_for(npad, 256);
 #define PP_SD_ARGS r[0], r[1], r[2], v[0], v[1], v[2], a[0], a[1], a[2], n, npad, dst, dt, half_dt2, \
                    cx, cy, cz, inv_l0, wrel
-    if (kind == STAGE_F32I) stage_drift_kernel<STAGE_F32I><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    if (kind == STAGE_F32IX2) stage_drift_kernel<STAGE_F32IX2><<<g, 256, 0, s>>>(PP_SD_ARGS);
+    else if (kind == STAGE_F32I) stage_drift_kernel<STAGE_F32I><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else if (kind == STAGE_F32) stage_drift_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else if (kind == STAGE_F32X2) stage_drift_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else stage_drift_kernel<STAGE_F64><<<g, 256, 0, s>>>(PP_SD_ARGS);

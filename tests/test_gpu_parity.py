@@ -117,6 +117,19 @@ def test_split_positions_meet_tolerance_on_close_pairs(n, radius):
                  report=f"split positions n={n}")
 
 
+def test_every_split_positions_variant():
+    n, R = 9000, 5e-6
+    pos = wl.uniform_sphere(n, R, seed=7 + n)
+    ref = oracle.fields(pos, 10.0, 1e-9)
+    names = capi.variants()
+    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32split.", "f32x2split."))]
+    assert len(chosen) >= 4
+    for v in chosen:
+        E = gpu_fields(pos, 10.0, 1e-9, positions=capi.PP_POS_SPLIT, variant=v)
+        check_fields(E, ref, tol=FORCE_TOL, bound=bound_for(pos, 10.0, 1e-9, split=True),
+                     report=f"split variant {names[v]}")
+
+
 def test_paper_lattice_fields():
     """The paper's 16^3 cube lattice (Sec. 2.1): all 4096 fields."""
     b = wl.PAPER_LATTICE
