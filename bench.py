@@ -54,6 +54,8 @@ def parse():
                     help="steps of the 64-bunch mix, batched and one bunch per launch (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the bounded serving trace (0 = skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 2^20-particle and all-FP64 comparison measurements")
     return ap.parse_args()
 
 
@@ -194,6 +196,41 @@ def cpu_baseline(seconds: float, bunch=WORKLOAD):
             "kind": "oracle",
             "sample": f"FP64 oracle fields at {m2} of {n} particles against all {n} sources "
                       f"({m2 * n:.3e} pairs, {el:.1f} s)"}
+
+
+def run_extras(sms: int, peak_tflops: float):
+    """Side measurements on the same GPU: the single-bunch force step at N = 2^20 (the
+    size the FP32 target is stated at) and the all-FP64 path on the benchmark bunch."""
+    import torch
+    from paper_2502_10640_gb300 import capi
+    out = {}
+    b = wl.SPHERE_1M
+    with capi.Simulation(b.n, b.w, b.dt, b.eps, tune="cache") as sim:
+        sim.load(b.positions())
+        sim.step(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        stream = torch.cuda.Stream()
+        sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
+        ev[0].record(stream)
+        sim.step(3)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        sec = ev[0].elapsed_time(ev[1]) / 1e3 / 3
+        pairs = float(b.n) ** 2 / sec
+        out["sphere_2p20"] = {"workload": b.name, "pairs_per_s": pairs, "ms_per_step": sec * 1e3,
+                              "frac_fp32_peak": FLOP_PER_PAIR * pairs / 1e12 / peak_tflops,
+                              "kernel": (sim.tuned or {}).get("variant_name")}
+    g = WORKLOAD
+    with capi.Simulation(g.n, g.w, g.dt, g.eps, acc=capi.PP_ACC_FP64_FULL) as sim:
+        sim.load(g.positions())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(1)
+        sec = time.perf_counter() - t0
+        out["fp64_path"] = {"workload": g.name, "pairs_per_s": float(g.n) ** 2 / sec,
+                            "ms_per_step": sec * 1e3,
+                            "note": "FP64 pair math and accumulation, one step"}
+    return out
 
 
 def run_batched(steps: int):
@@ -366,6 +403,10 @@ def run_ours(args):
 
     sim.close()
     batched = run_batched(args.batch_steps) if (args.batch_steps > 0 and world == 1) else None
+    extras = None
+    if not args.no_extras and world == 1:
+        pk, _ = load_peaks()
+        extras = run_extras(sms, fp32_peak_tflops(sms, float(pk.get("sm_max_mhz", 2070.0))))
     served = run_serving(args.serve_requests) if (args.serve_requests > 0 and world == 1) else None
     if rank != 0:
         if world > 1:
@@ -399,6 +440,8 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": csum,
     }
+    if extras:
+        line.update(extras)
     if batched:
         line["batched"] = batched
     if served:

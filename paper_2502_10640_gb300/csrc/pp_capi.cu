@@ -839,7 +839,7 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
             for (int q = 0; q < k; ++q) dup |= cand[q] == cand[k];
             if (dup) continue;
             c->split_override = cand[k];
-            // one untimed pass, then enough timed passes for about 5 ms (at least 2)
+            // one untimed pass, one pass to size the measurement, then the timed passes
             st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
             if (st != PP_OK) break;
             PP_CUDA(cudaEventRecord(e0, c->stream));
@@ -848,7 +848,8 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
             PP_CUDA(cudaEventSynchronize(e1));
             float first = 0.f;
             PP_CUDA(cudaEventElapsedTime(&first, e0, e1));
-            const int reps = std::max(2, std::min(20, (int)(5.0 / std::max(first, 1e-3f))));
+            // about 20 ms of timed passes per candidate (3 to 50 passes)
+            const int reps = std::max(3, std::min(50, (int)(20.0 / std::max(first, 1e-3f))));
             PP_CUDA(cudaEventRecord(e0, c->stream));
             for (int r = 0; r < reps && st == PP_OK; ++r)
                 st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
