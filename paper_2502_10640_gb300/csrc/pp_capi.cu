@@ -151,6 +151,38 @@ const Variant *pick_variant(const pp_ctx *c, int kind)
     return force_variant(c);
 }
 
+// Can at least one cluster of this variant be resident on the device?
+bool cluster_fits(const Variant &v)
+{
+    if (v.cluster > 8 &&
+        cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(v.cluster);
+    cfg.blockDim = dim3(v.T);
+    cfg.dynamicSmemBytes = v.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)v.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, v.fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n >= 1;
+}
+
 struct Plan {
     const Variant *v;
     int nib, nsplit, jchunk, grid, nipad;
@@ -188,6 +220,14 @@ Plan make_plan(pp_ctx *c, int kind)
         }
     }
     if (c->split_override > 0) best_s = std::min(c->split_override, tiles);
+    if (pl.v->cluster > 0) {
+        // one cluster per target block, one source chunk per CTA of the cluster
+        const int cl = pl.v->cluster;
+        pl.jchunk = ((tiles + cl - 1) / cl) * pl.v->tile;
+        pl.nsplit = cl;
+        pl.grid = pl.nib * cl;
+        return pl;
+    }
     const int chunk_tiles = (tiles + best_s - 1) / best_s;
     pl.jchunk = chunk_tiles * pl.v->tile;
     pl.nsplit = (tiles + chunk_tiles - 1) / chunk_tiles;
@@ -198,7 +238,9 @@ Plan make_plan(pp_ctx *c, int kind)
 pp_status ensure_workspace(pp_ctx *c, const Plan &pl)
 {
     const int ncomp = (pl.v->kind == KIND_PHI32) ? 1 : 3;
-    const size_t need = pl.nsplit > 1 ? (size_t)pl.nsplit * ncomp * pl.nipad * sizeof(double) : 0;
+    const size_t need = (pl.nsplit > 1 && pl.v->cluster == 0)
+                            ? (size_t)pl.nsplit * ncomp * pl.nipad * sizeof(double)
+                            : 0;
     if (need > c->partial_bytes) {
         if (c->partial) cudaFree(c->partial);
         c->partial = nullptr;
@@ -827,6 +869,7 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
         if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
             split_layout != (c->positions == PP_POS_SPLIT))
             continue;
+        if (vs[v].cluster > 0 && !cluster_fits(vs[v])) continue;   // cannot launch here
         c->variant_override = v;
         c->split_override = 0;
         const Plan base = make_plan(c, vs[v].kind);
@@ -834,7 +877,8 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
         int cand[4] = {base.nsplit, std::max(1, base.nsplit / 2), std::min(tiles, 2 * base.nsplit),
                        std::max(1, base.nsplit / 4)};
         st = stage_current(c, scratch, vs[v].stage);
-        for (int k = 0; k < 4 && st == PP_OK; ++k) {
+        const int ncand = vs[v].cluster > 0 ? 1 : 4;   // a cluster fixes the split
+        for (int k = 0; k < ncand && st == PP_OK; ++k) {
             bool dup = false;
             for (int q = 0; q < k; ++q) dup |= cand[q] == cand[k];
             if (dup) continue;

@@ -1018,4 +1018,147 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                                                               ay64[r], az64[r]);
 }
 
+
+// ---- j-split reduced through distributed shared memory -----------------------
+// A thread-block cluster of CL CTAs owns one block of BI targets; CTA rank q of
+// the cluster sums the q-th of CL source chunks into its shared-memory FP64
+// accumulators.  After a cluster barrier, rank 0 adds the CL partial sums from
+// its peers' shared memory in the fixed order q = 0..CL-1 (ld.shared::cluster)
+// and runs the epilogue; a second barrier keeps the peers' shared memory alive
+// until rank 0 has read it.  No global partials, fences or tickets: the
+// reduction costs two cluster barriers and CL distributed-shared-memory reads
+// per value, which shortens the per-step latency chain at small N.
+template <int T, int R, int TILE, int STAGES, int MINB, int CL>
+__global__ void __launch_bounds__(T, MINB) force_f32x2_cluster_kernel(const ForceArgs p)
+{
+    constexpr int BI = T * R;
+    static_assert(TILE % 2 == 0, "sources are consumed in pairs");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int rank = (int)cluster_ctarank();        // == blockIdx.x % CL
+    const int ib = blockIdx.x / CL;
+    const int i0 = ib * BI;
+    const int j0 = rank * p.jchunk;
+    const int j1 = min(j0 + p.jchunk, p.npad);
+    const int ntiles = j1 > j0 ? (j1 - j0) / TILE : 0;
+
+    Ring<float4, TILE, STAGES> rg{reinterpret_cast<float4 *>(smem_raw), nullptr, bar_full,
+                                  bar_empty};
+    double *sacc = reinterpret_cast<double *>(smem_raw + (size_t)STAGES * TILE * sizeof(float4));
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], T / 32);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        sacc[r * T + tid] = sacc[BI + r * T + tid] = sacc[2 * BI + r * T + tid] = 0.0;
+    __syncthreads();
+
+    const float *srcf = static_cast<const float *>(p.src);
+    f2_t X[R], Y[R], Z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        float x = -1e18f, y = -1e18f, z = -1e18f;
+        if (i < p.n) {
+            const float *q = srcf + 8 * (size_t)(i >> 1) + (i & 1);
+            x = q[0];
+            y = q[2];
+            z = q[4];
+        }
+        X[r] = f2_pack(x, x);
+        Y[r] = f2_pack(y, y);
+        Z[r] = f2_pack(z, z);
+    }
+    const f2_t EPS2 = f2_pack(p.eps2f, p.eps2f);
+    int issued = 0, seen = 0;
+    const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int) {
+            f2_t AX[R], AY[R], AZ[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
+#pragma unroll 2
+            for (int k = 0; k < TILE / 2; ++k) {
+                const float4 a = tile[2 * k];
+                const float4 b = tile[2 * k + 1];
+                const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const f2_t DX = f2_sub(X[r], XJ);
+                    const f2_t DY = f2_sub(Y[r], YJ);
+                    const f2_t DZ = f2_sub(Z[r], ZJ);
+                    const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
+                    float s0, s1;
+                    f2_unpack(S, s0, s1);
+                    const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
+                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
+                    AX[r] = f2_fma(INV3, DX, AX[r]);
+                    AY[r] = f2_fma(INV3, DY, AY[r]);
+                    AZ[r] = f2_fma(INV3, DZ, AZ[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float x0, x1, y0, y1, z0, z1;
+                f2_unpack(AX[r], x0, x1);
+                f2_unpack(AY[r], y0, y1);
+                f2_unpack(AZ[r], z0, z1);
+                float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
+                if (!isfinite(fx + fy + fz)) {
+                    float xs, ys, zs, dummy;
+                    f2_unpack(X[r], xs, dummy);
+                    f2_unpack(Y[r], ys, dummy);
+                    f2_unpack(Z[r], zs, dummy);
+                    const float3 f = tile_safe1_interleaved<TILE>(
+                        reinterpret_cast<const float *>(tile), nullptr, xs, ys, zs, 0.f, 0.f, 0.f,
+                        p.eps2f);
+                    fx = f.x;
+                    fy = f.y;
+                    fz = f.z;
+                }
+                sacc[r * T + tid] += (double)fx;
+                sacc[BI + r * T + tid] += (double)fy;
+                sacc[2 * BI + r * T + tid] += (double)fz;
+            }
+        });
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(p.err, 1);
+    }
+    __syncthreads();
+    if (s_abort) ring_drain(p, rg, issued, seen, ntiles);
+    cluster_sync();  // every CTA's partials (and abort flag) are visible to rank 0
+    if (rank == 0) {
+        int any_abort = 0;
+        for (int q = 0; q < CL; ++q) any_abort |= ld_peer_s32(peer_smem(&s_abort, (uint32_t)q));
+        if (!any_abort) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double t[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint32_t a0 = peer_smem(&sacc[c * BI + r * T + tid], 0);
+                    double acc = 0.0;
+                    for (int q = 0; q < CL; ++q) {
+                        // the same offset in CTA q: shared windows of a cluster are laid out
+                        // by rank, so map each peer explicitly
+                        acc += ld_peer_f64(q == 0 ? a0 : peer_smem(&sacc[c * BI + r * T + tid],
+                                                                   (uint32_t)q));
+                    }
+                    t[c] = acc;
+                }
+                finish_particle<STAGE_F32I>(p, i0 + r * T + tid, t[0], t[1], t[2]);
+            }
+        }
+    }
+    cluster_sync();  // keep every CTA's shared memory alive until rank 0 has read it
+}
+
 }  // namespace ppk

@@ -30,6 +30,8 @@ struct Variant {
     int T, R, tile, stages;
     const void *fn;
     size_t smem;  // dynamic shared memory bytes
+    int cluster;  // CTAs per thread-block cluster (0: no cluster; the j-split is then S
+                  // global-partial chunks chosen by the planner, else exactly `cluster`)
 };
 
 // Record the message pp_last_error() returns on this thread.

@@ -30,6 +30,15 @@ Variant make_f32x2(const char *name)
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
 }
 
+template <int T, int R, int TILE, int STAGES, int MINB, int CL>
+Variant make_cluster(const char *name)
+{
+    return Variant{name, KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R, TILE, STAGES,
+                   reinterpret_cast<const void *>(
+                       &force_f32x2_cluster_kernel<T, R, TILE, STAGES, MINB, CL>),
+                   (size_t)STAGES * TILE * sizeof(float4) + (size_t)3 * T * R * sizeof(double), CL};
+}
+
 template <int T, int R, int TILE, int STAGES>
 Variant make_phi(const char *name)
 {
@@ -65,6 +74,11 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
+    // j-split reduced through distributed shared memory of a thread-block cluster
+    make_cluster<64, 1, 128, 4, 8, 8>("f32x2cl8.dsmem.t64r1k128"),
+    make_cluster<64, 1, 128, 4, 8, 16>("f32x2cl16.dsmem.t64r1k128"),
+    make_cluster<128, 1, 128, 4, 8, 16>("f32x2cl16.dsmem.t128r1k128"),
+    make_cluster<128, 2, 128, 4, 4, 8>("f32x2cl8.dsmem.t128r2k128"),
     // packed pair math on hi/lo split positions
     make_f32x2<128, 2, 512, 3, 4, true, false, true>("f32x2split.sfold64.t128r2k512m4"),
     make_f32x2<128, 4, 256, 3, 4, true, false, true>("f32x2split.sfold64.t128r4k256m4"),
@@ -99,7 +113,26 @@ cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaS
     }
     ForceArgs copy = a;
     void *args[] = {&copy};
-    return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.T), args, v.smem, stream);
+    if (v.cluster <= 0) return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.T), args, v.smem, stream);
+    static bool cluster_configured[sizeof(kVariants) / sizeof(kVariants[0])] = {};
+    if (idx >= 0 && !cluster_configured[idx] && v.cluster > 8) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cluster_configured[idx] = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(v.T);
+    cfg.dynamicSmemBytes = v.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)v.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, v.fn, args);
 }
 
 // ---- O(N) kernels ----------------------------------------------------------

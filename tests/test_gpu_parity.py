@@ -155,8 +155,8 @@ def test_every_fp32_variant():
     # every FP64-fold kernel on single-float sources (scalar and packed f32x2)
     bound = bound_for(pos, 2.0, 0.0)
     names = capi.variants()
-    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32.fold64", "f32x2."))]
-    assert len(chosen) >= 7
+    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32.fold64", "f32x2.", "f32x2cl"))]
+    assert len(chosen) >= 11
     for v in chosen:
         check_fields(gpu_fields(pos, 2.0, 0.0, variant=v), ref, bound=bound,
                      report=f"variant={names[v]}")
