@@ -32,6 +32,7 @@
  *   - Calls on one context must not run concurrently from several threads.
  *   - Calls return after the work they enqueue has finished (the stream is
  *     synchronised), so a status reflects device-side errors as well.
+ *   - Host-side phases are marked with NVTX ranges named after the call.
  */
 #ifndef PP_GB300_H
 #define PP_GB300_H
@@ -78,7 +79,8 @@ enum {
     PP_OPT_STREAM = 2,         /* value: cudaStream_t cast to int64 (0 = the context's own)   */
     PP_OPT_SPLIT = 3,          /* value: j-split count S >= 1, or 0 for automatic              */
     PP_OPT_GRAPH_BLOCK = 4,    /* value: steps per captured CUDA graph (0 = plain launches)   */
-    PP_OPT_TIMEOUT_NS = 5,     /* value: limit of each device-side wait in ns (default 1e9)   */
+    PP_OPT_TIMEOUT_NS = 5,     /* value: limit of each device-side wait in ns (default 1e9, or
+                                  the environment variable PP_TIMEOUT_NS at creation)        */
     PP_OPT_VARIANT = 6,        /* value: force-kernel variant index (-1 = automatic)          */
     PP_OPT_POSITIONS = 7,      /* value: a pp_positions (FP32 pair paths only)                 */
     PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy, so

@@ -3,6 +3,7 @@
 // budget, with CUDA-graph step blocks.  C ABI in include/pp.h (pp_batch_*).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -281,6 +282,10 @@ pp_status pp_batch_create(int64_t budget_bytes, pp_batch **out)
     if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PP_ERR_CUDA, "cudaStreamCreate failed");
     b->stream = b->own_stream;
+    if (const char *env = std::getenv("PP_TIMEOUT_NS")) {
+        const long long t = std::atoll(env);
+        if (t >= 1000 && t <= 60000000000ll) b->timeout_ns = (uint64_t)t;
+    }
     const bool ok = cudaMalloc(&b->d_descs, kMaxBunches * sizeof(BunchDesc)) == cudaSuccess &&
                     cudaMalloc(&b->d_hdr, sizeof(BatchHeader)) == cudaSuccess &&
                     cudaMalloc(&b->d_init_desc, sizeof(BunchDesc)) == cudaSuccess &&
@@ -328,6 +333,7 @@ pp_status pp_batch_set_option(pp_batch *b, int key, int64_t value)
 pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softening,
                        const double *pos, const double *vel, int on_device, int *slot_out)
 {
+    NvtxRange nvtx_("pp_batch_add");
     if (!b || !pos || !slot_out) return bfail(PP_ERR_ARG, "null argument");
     if (N < 1 || N > (int64_t(1) << 28)) return bfail(PP_ERR_ARG, "N must be in [1, 2^28]");
     if (!(std::isfinite(w) && w > 0) || !(std::isfinite(dt) && dt > 0) ||
@@ -454,6 +460,7 @@ pp_status pp_batch_remove(pp_batch *b, int slot)
 
 pp_status pp_batch_step(pp_batch *b, int64_t nsteps)
 {
+    NvtxRange nvtx_("pp_batch_step");
     if (!b) return bfail(PP_ERR_ARG, "null batch");
     if (nsteps < 0) return bfail(PP_ERR_ARG, "nsteps must be >= 0");
     B_CUDA(cudaSetDevice(b->device));

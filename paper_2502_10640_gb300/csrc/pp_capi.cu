@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -549,6 +550,10 @@ pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **o
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PP_ERR_CUDA, "cudaStreamCreate failed");
     c->stream = c->own_stream;
+    if (const char *env = std::getenv("PP_TIMEOUT_NS")) {   // default bound of device waits
+        const long long t = std::atoll(env);
+        if (t >= 1000 && t <= 60000000000ll) c->timeout_ns = (uint64_t)t;
+    }
     const size_t np = (size_t)c->npad;
     c->stage_bytes = np * sizeof(double4);  // room for either staging type
     bool okm = cudaMalloc(&c->state, 9 * np * sizeof(double)) == cudaSuccess &&
@@ -646,6 +651,7 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
 
 pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int on_device)
 {
+    NvtxRange nvtx_("pp_load_particles");
     if (pp_status s = check_ctx(c)) return s;
     if (!pos) return fail(PP_ERR_ARG, "pos is null");
     PP_CUDA(cudaSetDevice(c->device));
@@ -738,6 +744,7 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
 pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const double *acc,
                        int64_t step, const double *frame, int on_device)
 {
+    NvtxRange nvtx_("pp_set_state");
     if (pp_status s = check_ctx(c)) return s;
     if (!pos || !vel || !acc) return fail(PP_ERR_ARG, "pos, vel and acc are required");
     PP_CUDA(cudaSetDevice(c->device));
@@ -777,6 +784,7 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
 pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t *step,
                        double *frame, int on_device)
 {
+    NvtxRange nvtx_("pp_get_state");
     if (pp_status s = check_ctx(c)) return s;
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
     PP_CUDA(cudaSetDevice(c->device));
@@ -802,6 +810,7 @@ pp_status pp_get_particles(pp_ctx *c, double *pos, double *vel, int on_device)
 
 pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
 {
+    NvtxRange nvtx_("pp_compute_fields");
     if (pp_status s = check_ctx(c)) return s;
     if (!E_out) return fail(PP_ERR_ARG, "E_out is null");
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
@@ -821,6 +830,7 @@ pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
 
 pp_status pp_step(pp_ctx *c, int64_t nsteps)
 {
+    NvtxRange nvtx_("pp_step");
     if (pp_status s = check_ctx(c)) return s;
     if (nsteps < 0) return fail(PP_ERR_ARG, "nsteps must be >= 0");
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
@@ -850,6 +860,7 @@ pp_status pp_step(pp_ctx *c, int64_t nsteps)
 
 pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
 {
+    NvtxRange nvtx_("pp_autotune");
     if (pp_status s = check_ctx(c)) return s;
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
     PP_CUDA(cudaSetDevice(c->device));
@@ -936,6 +947,7 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
 
 pp_status pp_diagnostics(pp_ctx *c, pp_diag *d, int with_pe)
 {
+    NvtxRange nvtx_("pp_diagnostics");
     if (pp_status s = check_ctx(c)) return s;
     if (!d) return fail(PP_ERR_ARG, "out is null");
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");

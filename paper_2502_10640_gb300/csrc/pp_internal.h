@@ -6,9 +6,21 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pp_force.cuh"
 
 namespace ppk {
+
+// NVTX range for the duration of a scope (visible under Nsight tools; a no-op
+// otherwise).  Marks the host-side phases: load, step blocks, fields,
+// diagnostics, autotuning, batch steps.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // CODATA 2018 (SI).  The paper prints no constants.
 constexpr double kE = 1.602176634e-19;      // elementary charge, C (exact)
