@@ -54,7 +54,7 @@ struct pp_ctx {
     double *state = nullptr;
     double *r[3] = {}, *v[3] = {}, *a[3] = {};
     void *stage[2] = {};           // float4 (or double4 for FP64 pair math) [npad]
-    size_t stage_bytes = 0;
+    size_t stage_bytes = 0;        // per buffer: 32 bytes per entry fits every layout
     double *aos = nullptr;         // [n][3] scratch for host transfers / outputs
     double *phi = nullptr;         // [n]
     double *wts = nullptr;         // per-particle weights [npad] (null: all equal to w)
@@ -694,7 +694,6 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
     if (c->acc == PP_ACC_KAHAN || c->positions == PP_POS_SPLIT)
         return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL "
                                 "with single positions");
-    const int old_kind = stage_kind(c);
     if (!w) {
         cudaFree(c->wts);
         cudaFree(c->wrel);
@@ -732,7 +731,6 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
     drop_graphs(c);
     if (!c->loaded) return PP_OK;
     // the acceleration belongs to the weights: recompute a(r) and restage r_{n+1}
-    (void)old_kind;
     pp_status st = pad_both(c);
     if (st == PP_OK) st = stage_current(c, c->stage[c->parity ^ 1], stage_kind(c));
     if (st == PP_OK)
