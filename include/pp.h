@@ -214,7 +214,8 @@ pp_status pp_fields_noalloc(int64_t N, double w, double softening, const double 
  * same alone or in any mix.  Device memory is admitted against the budget
  * given at creation (pp_batch_footprint says what one bunch takes).  Step
  * blocks of PP_OPT_GRAPH_BLOCK steps (even; default 16) replay a captured
- * CUDA graph.  Options: PP_OPT_STREAM, PP_OPT_GRAPH_BLOCK, PP_OPT_TIMEOUT_NS.
+ * CUDA graph.  Options: PP_OPT_STREAM, PP_OPT_GRAPH_BLOCK, PP_OPT_TIMEOUT_NS,
+ * PP_OPT_TEST_SKIP_COPY.
  * Bunches use single FP32 staging and the FP64 fold (PP_ACC_FP64FOLD).
  */
 typedef struct pp_batch pp_batch;

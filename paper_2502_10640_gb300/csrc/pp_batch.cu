@@ -96,6 +96,7 @@ struct pp_batch {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     uint64_t timeout_ns = 1000000000ull;
+    int skip_copy = 0;                // test hook for the next launch (PP_OPT_TEST_SKIP_COPY)
     std::vector<int> order;           // active slots in table order
 };
 
@@ -160,8 +161,10 @@ pp_status launch_batch(pp_batch *b, const BunchDesc *descs, const BatchHeader *h
     int *err = b->d_err;
     unsigned *queue = b->d_queue;
     unsigned long long tmo = b->timeout_ns;
+    int skip = b->skip_copy;
+    b->skip_copy = 0;
     void *args[] = {(void *)&descs, (void *)&hdr, (void *)&queue, (void *)&step_k, (void *)&err,
-                    (void *)&tmo};
+                    (void *)&tmo, (void *)&skip};
     B_CUDA(cudaLaunchKernel(fn, dim3(b->grid), dim3(kBatchT), args, batch_smem(), b->stream));
     return PP_OK;
 }
@@ -320,6 +323,9 @@ pp_status pp_batch_set_option(pp_batch *b, int key, int64_t value)
         drop_graph(b);
         b->graph_block = (int)value;
         return PP_OK;
+    case PP_OPT_TEST_SKIP_COPY:
+        b->skip_copy = value ? 1 : 0;
+        return PP_OK;
     case PP_OPT_TIMEOUT_NS:
         if (value < 1000 || value > 60000000000ll) return bfail(PP_ERR_ARG, "timeout out of range");
         drop_graph(b);
@@ -470,7 +476,7 @@ pp_status pp_batch_step(pp_batch *b, int64_t nsteps)
     if (b->order.empty() || nsteps == 0) return PP_OK;
     int64_t left = nsteps;
     const int gb = b->graph_block;
-    if (gb > 0 && (gb % 2) == 0 && left >= gb && b->stream != nullptr) {
+    if (gb > 0 && (gb % 2) == 0 && left >= gb && b->stream != nullptr && !b->skip_copy) {
         if (!b->graph || b->graph_steps != gb) {
             drop_graph(b);
             cudaGraph_t g = nullptr;

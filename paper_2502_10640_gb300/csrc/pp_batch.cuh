@@ -41,7 +41,8 @@ struct BatchHeader {
 template <int T, int R, int TILE, int STAGES, int MINB>
 __global__ void __launch_bounds__(T, MINB)
     batch_f32x2_kernel(const BunchDesc *__restrict__ descs, const BatchHeader *__restrict__ hdr,
-                       unsigned *queue, int step_k, int *err, unsigned long long timeout_ns)
+                       unsigned *queue, int step_k, int *err, unsigned long long timeout_ns,
+                       int skip_copy)
 {
     constexpr int BI = T * R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(T, MINB)
         p.inv_l0 = d.inv_l0;
         p.err = err;
         p.timeout_ns = timeout_ns;
+        p.skip_copy = skip_copy;   // test hook: CTA 0 withholds the last tile of its items
 
         const int i0 = ib * BI;
         const int j0 = split * p.jchunk;

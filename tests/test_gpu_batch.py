@@ -140,3 +140,27 @@ def test_batch_rejects_bad_input():
         with pytest.raises(capi.PPError) as e:
             b.remove(3)
         assert e.value.status == capi.PP_ERR_ARG
+
+
+def test_batch_bounded_wait_reports_timeout():
+    """A withheld tile copy in the persistent batch kernel: the step returns PP_ERR_TIMEOUT
+    (no fault, no hang), the bunches' states are reported unspecified, and the batch accepts
+    and steps new bunches afterwards."""
+    x = BUNCHES[1]
+    with capi.Batch(BIG) as b:
+        b.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
+        s0 = b.add(x["pos"], x["w"], x["dt"], x["eps"])
+        b.set_option(capi.PP_OPT_TEST_SKIP_COPY, 1)
+        with pytest.raises(capi.PPError) as e:
+            b.step(2)
+        assert e.value.status == capi.PP_ERR_TIMEOUT
+        with pytest.raises(capi.PPError) as e:
+            b.state(s0, x["n"])
+        assert e.value.status == capi.PP_ERR_STATE
+        b.remove(s0)
+        s1 = b.add(x["pos"], x["w"], x["dt"], x["eps"])
+        b.step(3)
+        got = b.state(s1, x["n"])
+    ref = _run([x], 3)[0]
+    for a, c in zip(got[:3], ref[:3]):
+        assert np.array_equal(a, c)

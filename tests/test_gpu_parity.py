@@ -363,12 +363,18 @@ def test_invalid_arguments_and_states():
         assert e.value.status == capi.PP_ERR_ARG
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers():
+@pytest.mark.parametrize("variant", [None, "f32.fold64.t128r2k128", "f32x2.sfold64.t128r4k512m4",
+                                     "f32x2cl8.dsmem.t64r1k128"])
+def test_bounded_wait_reports_timeout_and_context_recovers(variant):
     """A withheld tile copy makes the kernel's bounded waits run out: the call returns
-    PP_ERR_TIMEOUT (no fault, no hang) and the context works again after a reload."""
+    PP_ERR_TIMEOUT (no fault, no hang) and the context works again after a reload.
+    Covered for the default plan, a scalar kernel, the shared-memory-fold packed kernel
+    and the thread-block-cluster kernel (whose CTAs still meet at both cluster barriers)."""
     n = 3000
     pos = wl.gaussian_bunch(n, 2e-6, seed=41)
     with capi.Simulation(n, 1.0, 1e-15, 1e-9) as sim:
+        if variant is not None:
+            sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index(variant))
         sim.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
         sim.load(pos)
         sim.set_option(capi.PP_OPT_TEST_SKIP_COPY, 1)
@@ -380,7 +386,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
         assert e.value.status == capi.PP_ERR_STATE
         sim.load(pos)
         check_fields(sim.fields(), oracle.fields(pos, 1.0, 1e-9), tol=1e-4,
-                     bound=bound_for(pos, 1.0, 1e-9), report="after timeout")
+                     bound=bound_for(pos, 1.0, 1e-9), report=f"after timeout {variant}")
 
 
 def test_gaussian_65536_sampled_forces():
