@@ -64,7 +64,7 @@ struct ForceArgs {
     double cx, cy, cz, inv_l0;
     int *err;               // device error word (bit 0: a wait ran out)
     unsigned long long timeout_ns;
-    int skip_copy;          // test hook: CTA 0 withholds its last tile copy
+    int skip_copy;          // test hook: 1 = CTA 0 withholds its last tile copy, 2 = this CTA does
 };
 
 // ---- FP64 push arithmetic, written so that no multiply-add is fused: the
@@ -207,6 +207,12 @@ struct Ring {
     uint64_t *empty;
 };
 
+// Test hook (PP_OPT_TEST_SKIP_COPY): is the copy of local tile t withheld?
+__device__ __forceinline__ bool copy_withheld(const ForceArgs &p, int t, int ntiles)
+{
+    return t == ntiles - 1 && (p.skip_copy == 2 || (p.skip_copy == 1 && blockIdx.x == 0));
+}
+
 // Warp-uniform bounded wait: lane 0 waits (bounded), the verdict is shared
 // with the warp, then every lane observes the completed phase itself (which
 // gives each thread acquire ordering on the bulk-copied data).  All lanes
@@ -247,7 +253,7 @@ __device__ __forceinline__ bool run_tiles(const ForceArgs &p,
     auto issue = [&](int t) {
         const int s = (g0 + t) % STAGES;
         mbar_arrive_expect_tx(&rg.full[s], TWO ? 2 * kBytes : kBytes);
-        const bool withhold = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
+        const bool withhold = copy_withheld(p, t, ntiles);
         if (!withhold) {
             const size_t off = (size_t)j0 + (size_t)t * TILE;
             bulk_g2s(rg.buf + s * TILE, src + off, kBytes, &rg.full[s]);
@@ -317,7 +323,7 @@ __device__ __forceinline__ void ring_drain(const ForceArgs &p,
 {
     if (threadIdx.x != 0) return;
     for (int t = seen; t < issued; ++t) {
-        const bool withheld = p.skip_copy && blockIdx.x == 0 && t == ntiles - 1;
+        const bool withheld = copy_withheld(p, t, ntiles);
         if (withheld) continue;
         const int g = g0 + t;
         mbar_wait_bounded(&rg.full[g % STAGES], (g / STAGES) & 1, p.timeout_ns);
