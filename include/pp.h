@@ -247,8 +247,8 @@ pp_status pp_batch_step(pp_batch *b, int64_t nsteps);
 pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, double *acc,
                              int64_t *step, int on_device);
 
-/* Moments of one bunch (as pp_diagnostics; pe is NaN). */
-pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *out);
+/* Diagnostics of one bunch, as pp_diagnostics (with_pe = 0 sets pe to NaN). */
+pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *out, int with_pe);
 
 /* Active bunches, device bytes in use and the budget (any pointer may be NULL). */
 pp_status pp_batch_info(pp_batch *b, int64_t *active, int64_t *bytes_used, int64_t *budget);

@@ -105,7 +105,8 @@ SIGNATURES = [
     ("pp_batch_step", ctypes.c_int, [_CTX, _I64]),
     ("pp_batch_get_state", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(_I64),
                                           ctypes.c_int]),
-    ("pp_batch_diagnostics", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(pp_diag)]),
+    ("pp_batch_diagnostics", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(pp_diag),
+                                            ctypes.c_int]),
     ("pp_batch_info", ctypes.c_int, [_CTX, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                      ctypes.POINTER(_I64)]),
     ("pp_batch_destroy", ctypes.c_int, [_CTX]),
@@ -378,9 +379,10 @@ class Batch:
                                          acc.ctypes.data, ctypes.byref(step), 0))
         return pos, vel, acc, step.value
 
-    def diagnostics(self, slot: int) -> dict:
+    def diagnostics(self, slot: int, with_pe: bool = False) -> dict:
         d = pp_diag()
-        _check(load().pp_batch_diagnostics(self.b, int(slot), ctypes.byref(d)))
+        _check(load().pp_batch_diagnostics(self.b, int(slot), ctypes.byref(d),
+                                           1 if with_pe else 0))
         return d.as_dict()
 
     def info(self) -> dict:

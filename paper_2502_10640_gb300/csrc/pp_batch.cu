@@ -212,6 +212,77 @@ pp_status slot_moments(pp_batch *b, Slot &s, int pass, double cx, double cy, dou
     return PP_OK;
 }
 
+// Potential energy of one bunch: phi'_i = sum_{j != i} 1/|r'_ij| by the FP32 pair
+// kernel on freshly staged positions (scratch allocated for the call), then
+// PE = 1/2 k e^2 w^2 / L0 * sum_i phi'_i.
+pp_status slot_potential(pp_batch *b, Slot &s, double *pe)
+{
+    int count = 0;
+    const Variant *vs = variants(&count);
+    const Variant *v = nullptr;
+    for (int i = 0; i < count; ++i)
+        if (std::strcmp(vs[i].name, "phi32.fold64.t256r2k256") == 0) v = &vs[i];
+    if (!v) return bfail(PP_ERR_STATE, "potential kernel missing");
+    const int n = (int)s.n, npad = s.L.npad, BI = v->T * v->R;
+    const int nib = (n + BI - 1) / BI, tiles = npad / v->tile;
+    int S = std::min(tiles, std::max(1, (4 * b->sms + nib - 1) / nib));
+    const int chunk_tiles = (tiles + S - 1) / S;
+    S = (tiles + chunk_tiles - 1) / chunk_tiles;
+    float4 *stage = nullptr;
+    double *phi = nullptr, *partial = nullptr;
+    unsigned *tickets = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(stage);
+        cudaFree(phi);
+        cudaFree(partial);
+        cudaFree(tickets);
+    };
+    if (cudaMalloc(&stage, (size_t)npad * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&phi, (size_t)npad * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&partial, (size_t)S * nib * BI * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&tickets, (size_t)nib * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return bfail(PP_ERR_NOMEM, "cannot allocate the potential-energy scratch");
+    }
+    ForceArgs a{};
+    a.src = stage;
+    a.n = n;
+    a.npad = npad;
+    a.nib = nib;
+    a.nsplit = S;
+    a.jchunk = chunk_tiles * v->tile;
+    a.mode = MODE_PHI;
+    const double epsl = s.eps / s.l0;
+    a.eps2d = epsl * epsl;
+    a.eps2f = (float)a.eps2d;
+    a.partial = partial;
+    a.tickets = tickets;
+    a.nipad = nib * BI;
+    a.out = phi;
+    a.err = b->d_err;
+    a.timeout_ns = b->timeout_ns;
+    double m[kMomSlots];
+    int flags[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(tickets, 0, (size_t)nib * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess)
+        e = launch_stage(s.r[0], s.r[1], s.r[2], n, npad, stage, STAGE_F32, s.cx, s.cy, s.cz,
+                         1.0 / s.l0, b->stream);
+    if (e == cudaSuccess) e = launch_variant(*v, a, nib * S, b->stream);
+    if (e == cudaSuccess)
+        e = launch_moments(2, n, phi, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0,
+                           b->mom_partials, b->mom_out, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m, b->mom_out, sizeof(m), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cleanup();
+    if (e != cudaSuccess) return bcuda(e, "potential-energy pass");
+    if (pp_status st = read_errors(b, flags)) return st;
+    if (flags[0]) return bfail(PP_ERR_TIMEOUT, "a device-side wait ran out of time");
+    *pe = 0.5 * kCoulomb * kE * kE * s.w * s.w / s.l0 * m[0];
+    return PP_OK;
+}
+
 pp_status check_slot(const pp_batch *b, int slot)
 {
     if (!b) return bfail(PP_ERR_ARG, "null batch");
@@ -539,7 +610,7 @@ pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, do
     return PP_OK;
 }
 
-pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *d)
+pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *d, int with_pe)
 {
     if (pp_status st = check_slot(b, slot)) return st;
     if (!d) return bfail(PP_ERR_ARG, "out is null");
@@ -557,6 +628,9 @@ pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *d)
     d->rms_radius = std::sqrt(m1[0] / n);
     d->ke = 0.5 * mw * m1[1];
     d->pe = NAN;
+    if (with_pe) {
+        if (pp_status st = slot_potential(b, s, &d->pe)) return st;
+    }
     d->px = mw * m1[2];
     d->py = mw * m1[3];
     d->pz = mw * m1[4];

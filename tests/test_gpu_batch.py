@@ -50,10 +50,11 @@ def test_batch_runs_match_oracle():
             assert rel(p - x["pos"], pr - x["pos"]) <= TOL
             assert rel(v, vr) <= TOL
             assert rel(a, ar) <= TOL
-            d = b.diagnostics(s)
+            d = b.diagnostics(s, with_pe=True)
             dr = oracle.diagnostics(pr, vr, x["w"])
             assert abs(d["rms_radius"] / dr["rms_radius"] - 1) <= TOL
             assert abs(d["ke"] / dr["ke"] - 1) <= TOL
+            assert abs(d["pe"] / oracle.potential_energy(pr, x["w"], x["eps"]) - 1) <= TOL
 
 
 def _run(members, steps, graph_block=0, add_order=None):

@@ -98,3 +98,26 @@ def test_paper_lattice_experiment_series_matches_oracle():
             got = run["series"][key][k + 1]
             assert abs(got / d[key] - 1) <= 1e-5, (k, key, got, d[key])
         assert abs(run["series"]["x_max"][k + 1] / d["x_max"] - 1) <= 1e-6
+
+
+def test_gaussian_65536_radius_agrees_with_the_fp64_gpu_path():
+    """The benchmark bunch for 100 steps with FP32 pair math and with the all-FP64 path
+    (itself within 1e-12 of the oracle's fields): RMS radius growth and momenta agree."""
+    b = wl.GAUSSIAN_65536
+    pos0 = b.positions()
+    out = {}
+    for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_FP64_FULL):
+        with capi.Simulation(b.n, b.w, b.dt, b.eps, acc=acc) as sim:
+            sim.load(pos0)
+            d0 = sim.diagnostics(with_pe=False)
+            sim.step(100)
+            d1 = sim.diagnostics(with_pe=False)
+            p, v, _, _, _ = sim.state()
+        out[acc] = (d0, d1, p, v)
+    (d0a, d1a, pa, va), (d0b, d1b, pb, vb) = out[capi.PP_ACC_FP64FOLD], out[capi.PP_ACC_FP64_FULL]
+    assert abs(d1a["rms_radius"] / d1b["rms_radius"] - 1) <= 1e-5
+    grow_a = d1a["rms_radius"] - d0a["rms_radius"]
+    grow_b = d1b["rms_radius"] - d0b["rms_radius"]
+    assert abs(grow_a / grow_b - 1) <= 1e-4
+    assert rel(va, vb) <= 1e-5
+    assert rel(pa - pos0, pb - pos0) <= 1e-5
