@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -184,6 +185,30 @@ bool cluster_fits(const Variant &v)
     return n >= 1;
 }
 
+// Resident CTAs per SM of a variant (queried once per variant and process).
+int resident_ctas(const Variant &v)
+{
+    static std::mutex lock;
+    static std::vector<int> cache;
+    int count = 0;
+    const Variant *vs = variants(&count);
+    const int idx = (int)(&v - vs);
+    std::lock_guard<std::mutex> g(lock);
+    if ((int)cache.size() < count) cache.assign(count, 0);
+    if (idx < 0 || idx >= count) return 1;
+    if (cache[idx] == 0) {
+        int occ = 0;
+        cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.T, v.smem) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        cache[idx] = occ;
+    }
+    return cache[idx];
+}
+
 struct Plan {
     const Variant *v;
     int nib, nsplit, jchunk, grid, nipad;
@@ -199,9 +224,7 @@ Plan make_plan(pp_ctx *c, int kind)
     pl.nib = (int)((c->n + BI - 1) / BI);
     pl.nipad = pl.nib * BI;
     const int tiles = c->npad / pl.v->tile;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl.v->fn, pl.v->T, pl.v->smem);
-    if (occ < 1) occ = 1;
+    const int occ = resident_ctas(*pl.v);
     const int64_t slots = (int64_t)c->sms * occ;
     int best_s = 1;
     double best_cost = 1e300;
