@@ -79,11 +79,36 @@ class Server:
         self.active: dict[int, dict] = {}
         self.results: list[ServeResult] = []
         self.rejected: list[int] = []
+        self.cancelled: list[int] = []
+        self._cancel: set[int] = set()
         self.pairs = 0.0
         self.blocks = 0
 
     def close(self):
         self.batch.close()
+
+    def cancel(self, rid: int):
+        """Cancel a request: dropped if it waits, removed (memory freed) at the next block
+        boundary if it runs.  Unknown or finished ids are ignored."""
+        self._cancel.add(rid)
+
+    def _apply_cancellations(self):
+        if not self._cancel:
+            return
+        kept = collections.deque()
+        for r in self.pending:
+            if r.rid in self._cancel:
+                self.cancelled.append(r.rid)
+                self._cancel.discard(r.rid)
+            else:
+                kept.append(r)
+        self.pending = kept
+        for slot in [s for s, a in self.active.items() if a["req"].rid in self._cancel]:
+            a = self.active.pop(slot)
+            self.batch.remove(slot)
+            self.cancelled.append(a["req"].rid)
+            self._cancel.discard(a["req"].rid)
+        # ids not seen yet stay marked: they are dropped when they arrive
 
     def _free(self) -> int:
         return self.budget - self.batch.info()["bytes_used"]
@@ -116,14 +141,23 @@ class Server:
             self.results.append(ServeResult(r.rid, r.n, step, r.arrival, a["admitted"],
                                             self.clock() - self.t0, pos, vel, acc, diag))
 
-    def run(self, requests: list[ServeRequest]) -> dict:
-        """Serve a trace to completion; returns the latency/throughput report."""
+    def run(self, requests: list[ServeRequest], on_block=None) -> dict:
+        """Serve a trace to completion; returns the latency/throughput report.
+
+        on_block(server), if given, is called after every step block (for example to
+        cancel requests)."""
         arrivals = collections.deque(sorted(requests, key=lambda r: r.arrival))
         self.t0 = self.clock()
         while arrivals or self.pending or self.active:
             now = self.clock() - self.t0
             while arrivals and arrivals[0].arrival <= now:
-                self.pending.append(arrivals.popleft())
+                r = arrivals.popleft()
+                if r.rid in self._cancel:
+                    self.cancelled.append(r.rid)
+                    self._cancel.discard(r.rid)
+                    continue
+                self.pending.append(r)
+            self._apply_cancellations()
             self._admit(now)
             # requests that reached zero steps (steps = 0) finish at once
             self._retire(now)
@@ -140,10 +174,13 @@ class Server:
                 a["left"] -= block
                 self.pairs += float(a["req"].n) ** 2 * block
             self._retire(self.clock() - self.t0)
+            if on_block is not None:
+                on_block(self)
         wall = self.clock() - self.t0
         lat = [r.latency for r in self.results]
         rep = {"requests": len(requests), "completed": len(self.results),
-               "rejected": len(self.rejected), "wall_s": wall, "blocks": self.blocks,
+               "rejected": len(self.rejected), "cancelled": len(self.cancelled),
+               "wall_s": wall, "blocks": self.blocks,
                "pairs": self.pairs, "pairs_per_s": self.pairs / wall if wall > 0 else float("nan")}
         if lat:
             rep.update({"p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),

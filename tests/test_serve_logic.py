@@ -122,3 +122,22 @@ def test_percentile_nearest_rank():
     assert serve.percentile([3, 1, 2], 50) == 2
     assert serve.percentile(list(range(1, 101)), 99) == 99
     assert serve.percentile([5.0], 99) == 5.0
+
+
+def test_cancel_waiting_and_running_requests(fake):
+    clock, made = fake
+    srv = serve.Server(budget_bytes=100 * 100, block_steps=4, clock=clock, sleep=clock.sleep)
+    trace = [req(0, 0.0, 60, 40), req(1, 0.0, 60, 4), req(2, 0.0, 10, 8), req(3, 5.0, 10, 4)]
+
+    def after_block(s):
+        if s.blocks == 1:
+            s.cancel(0)          # running: removed at this boundary, its memory freed
+            s.cancel(1)          # waiting for memory: dropped
+            s.cancel(3)          # not arrived yet: dropped on arrival
+    rep = srv.run(trace, on_block=after_block)
+    b = made[0]
+    assert sorted(srv.cancelled) == [0, 1, 3]
+    assert rep["cancelled"] == 3 and rep["completed"] == 1
+    assert [r.rid for r in srv.results] == [2]
+    assert ("remove", 0) in b.log
+    assert all(e[2] != 60 or e[1] == 0 for e in b.log if e[0] == "add")   # 1 never admitted
