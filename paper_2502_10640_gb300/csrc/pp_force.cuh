@@ -854,7 +854,7 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
 // separation as (hi_i - hi_j) + (lo_i - lo_j): three f32x2 operations per
 // component instead of one.
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
     constexpr int BI = T * R;
@@ -929,7 +929,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
             f2_t AX[R], AY[R], AZ[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
-#pragma unroll 2
+#pragma unroll UNROLL
             for (int k = 0; k < TILE / 2; ++k) {
                 const float4 a = tile[2 * k];       // x0 x1 y0 y1
                 const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1

@@ -19,13 +19,14 @@ Variant make_f32(const char *name)
 }
 
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2>
 Variant make_f32x2(const char *name)
 {
     return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, ACC_FP64FOLD,
                    SPLITPOS ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
-                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS>),
+                       &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS,
+                                           UNROLL>),
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1) +
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
 }
@@ -72,6 +73,7 @@ const Variant kVariants[] = {
     make_f32x2<128, 4, 256, 4, 4, true>("f32x2.sfold64.t128r4k256m4"),
     make_f32x2<128, 4, 512, 3, 5, true>("f32x2.sfold64.t128r4k512m5"),
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
+    make_f32x2<128, 4, 512, 3, 4, true, false, false, 1>("f32x2.sfold64.t128r4k512m4u1"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
     // j-split reduced through distributed shared memory of a thread-block cluster
