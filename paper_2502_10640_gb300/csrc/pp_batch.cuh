@@ -139,48 +139,14 @@ __global__ void __launch_bounds__(T, MINB)
             p, rg, j0, ntiles, issued, seen,
             [&](const float4 *tile, const float4 *, int) {
                 f2_t AX[R], AY[R], AZ[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
-#pragma unroll 2
-                for (int k = 0; k < TILE / 2; ++k) {
-                    const float4 a = tile[2 * k];
-                    const float4 b = tile[2 * k + 1];
-                    const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w),
-                               ZJ = f2_pack(b.x, b.y);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const f2_t DX = f2_sub(X[r], XJ);
-                        const f2_t DY = f2_sub(Y[r], YJ);
-                        const f2_t DZ = f2_sub(Z[r], ZJ);
-                        const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
-                        float s0, s1;
-                        f2_unpack(S, s0, s1);
-                        const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
-                        const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
-                        AX[r] = f2_fma(INV3, DX, AX[r]);
-                        AY[r] = f2_fma(INV3, DY, AY[r]);
-                        AZ[r] = f2_fma(INV3, DZ, AZ[r]);
-                    }
-                }
+                tile_packed<R, TILE, false, false, 2>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX,
+                                                      AY, AZ);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    float x0, x1, y0, y1, z0, z1;
-                    f2_unpack(AX[r], x0, x1);
-                    f2_unpack(AY[r], y0, y1);
-                    f2_unpack(AZ[r], z0, z1);
-                    float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
-                    if (!isfinite(fx + fy + fz)) {
-                        float xs, ys, zs, dummy;
-                        f2_unpack(X[r], xs, dummy);
-                        f2_unpack(Y[r], ys, dummy);
-                        f2_unpack(Z[r], zs, dummy);
-                        const float3 f = tile_safe1_interleaved<TILE>(
-                            reinterpret_cast<const float *>(tile), nullptr, xs, ys, zs, 0.f, 0.f,
-                            0.f, p.eps2f);
-                        fx = f.x;
-                        fy = f.y;
-                        fz = f.z;
-                    }
+                    const float3 f = tile_partial<TILE, false, false>(
+                        AX[r], AY[r], AZ[r], tile, nullptr, X[r], Y[r], Z[r], X[r], Y[r], Z[r],
+                        p.eps2f);
+                    const float fx = f.x, fy = f.y, fz = f.z;
                     sacc[r * T + tid] += (double)fx;
                     sacc[BI + r * T + tid] += (double)fy;
                     sacc[2 * BI + r * T + tid] += (double)fz;

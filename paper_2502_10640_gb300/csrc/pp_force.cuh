@@ -845,6 +845,84 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
     return make_float3(ax, ay, az);
 }
 
+
+// One tile of the packed pair loop: TILE interleaved sources, two per f32x2
+// operation, against R targets.  AX/AY/AZ receive each target's partial sums
+// over the even (low lane) and odd (high lane) sources of the tile.
+template <int R, int TILE, bool WEIGHTED, bool SPLITPOS, int UNROLL>
+__device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
+                                            const float4 *__restrict__ tlo, const f2_t (&X)[R],
+                                            const f2_t (&Y)[R], const f2_t (&Z)[R],
+                                            const f2_t (&XL)[R], const f2_t (&YL)[R],
+                                            const f2_t (&ZL)[R], f2_t EPS2, f2_t (&AX)[R],
+                                            f2_t (&AY)[R], f2_t (&AZ)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
+#pragma unroll UNROLL
+    for (int k = 0; k < TILE / 2; ++k) {
+        const float4 a = tile[2 * k];       // x0 x1 y0 y1
+        const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1
+        const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
+        const f2_t WJ = f2_pack(b.z, b.w);
+        f2_t XJL = 0ull, YJL = 0ull, ZJL = 0ull;
+        if (SPLITPOS) {
+            const float4 al = tlo[2 * k];
+            const float4 bl = tlo[2 * k + 1];
+            XJL = f2_pack(al.x, al.y);
+            YJL = f2_pack(al.z, al.w);
+            ZJL = f2_pack(bl.x, bl.y);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            f2_t DX = f2_sub(X[r], XJ);
+            f2_t DY = f2_sub(Y[r], YJ);
+            f2_t DZ = f2_sub(Z[r], ZJ);
+            if (SPLITPOS) {
+                DX = f2_add(DX, f2_sub(XL[r], XJL));
+                DY = f2_add(DY, f2_sub(YL[r], YJL));
+                DZ = f2_add(DZ, f2_sub(ZL[r], ZJL));
+            }
+            const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
+            float s0, s1;
+            f2_unpack(S, s0, s1);
+            const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
+            const f2_t INV3 = WEIGHTED ? f2_mul(f2_mul(f2_mul(INV, INV), INV), WJ)
+                                       : f2_mul(f2_mul(INV, INV), INV);
+            AX[r] = f2_fma(INV3, DX, AX[r]);
+            AY[r] = f2_fma(INV3, DY, AY[r]);
+            AZ[r] = f2_fma(INV3, DZ, AZ[r]);
+        }
+    }
+}
+
+// Tile partial of one target: the two lanes added; a non-finite result (a pair
+// with s == 0) is recomputed by the scalar loop that skips zero-distance pairs.
+template <int TILE, bool WEIGHTED, bool SPLITPOS>
+__device__ __forceinline__ float3 tile_partial(f2_t AX, f2_t AY, f2_t AZ, const float4 *tile,
+                                               const float4 *tlo, f2_t X, f2_t Y, f2_t Z, f2_t XL,
+                                               f2_t YL, f2_t ZL, float eps2)
+{
+    float x0, x1, y0, y1, z0, z1;
+    f2_unpack(AX, x0, x1);
+    f2_unpack(AY, y0, y1);
+    f2_unpack(AZ, z0, z1);
+    float3 f = make_float3(x0 + x1, y0 + y1, z0 + z1);
+    if (!isfinite(f.x + f.y + f.z)) {
+        float xs, ys, zs, xl, yl, zl, dummy;
+        f2_unpack(X, xs, dummy);
+        f2_unpack(Y, ys, dummy);
+        f2_unpack(Z, zs, dummy);
+        f2_unpack(XL, xl, dummy);
+        f2_unpack(YL, yl, dummy);
+        f2_unpack(ZL, zl, dummy);
+        f = tile_safe1_interleaved<TILE, WEIGHTED, SPLITPOS>(
+            reinterpret_cast<const float *>(tile), reinterpret_cast<const float *>(tlo), xs, ys,
+            zs, xl, yl, zl, eps2);
+    }
+    return f;
+}
+
 // SMEM_ACC keeps the FP64 fold accumulators in shared memory (BI x 3 doubles
 // per CTA) instead of registers, trading a shared load/store per fold for
 // fewer registers and so more resident warps.
@@ -927,65 +1005,13 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     const bool ok = run_tiles<float4, T, TILE, STAGES, SPLITPOS>(
         p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int) {
             f2_t AX[R], AY[R], AZ[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
-#pragma unroll UNROLL
-            for (int k = 0; k < TILE / 2; ++k) {
-                const float4 a = tile[2 * k];       // x0 x1 y0 y1
-                const float4 b = tile[2 * k + 1];   // z0 z1 w0 w1
-                const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
-                const f2_t WJ = f2_pack(b.z, b.w);
-                f2_t XJL = 0ull, YJL = 0ull, ZJL = 0ull;
-                if (SPLITPOS) {
-                    const float4 al = tlo[2 * k];
-                    const float4 bl = tlo[2 * k + 1];
-                    XJL = f2_pack(al.x, al.y);
-                    YJL = f2_pack(al.z, al.w);
-                    ZJL = f2_pack(bl.x, bl.y);
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    f2_t DX = f2_sub(X[r], XJ);
-                    f2_t DY = f2_sub(Y[r], YJ);
-                    f2_t DZ = f2_sub(Z[r], ZJ);
-                    if (SPLITPOS) {
-                        DX = f2_add(DX, f2_sub(XL[r], XJL));
-                        DY = f2_add(DY, f2_sub(YL[r], YJL));
-                        DZ = f2_add(DZ, f2_sub(ZL[r], ZJL));
-                    }
-                    const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
-                    float s0, s1;
-                    f2_unpack(S, s0, s1);
-                    const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
-                    const f2_t INV3 = WEIGHTED ? f2_mul(f2_mul(f2_mul(INV, INV), INV), WJ)
-                                               : f2_mul(f2_mul(INV, INV), INV);
-                    AX[r] = f2_fma(INV3, DX, AX[r]);
-                    AY[r] = f2_fma(INV3, DY, AY[r]);
-                    AZ[r] = f2_fma(INV3, DZ, AZ[r]);
-                }
-            }
+            tile_packed<R, TILE, WEIGHTED, SPLITPOS, UNROLL>(tile, tlo, X, Y, Z, XL, YL, ZL, EPS2,
+                                                            AX, AY, AZ);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float x0, x1, y0, y1, z0, z1;
-                f2_unpack(AX[r], x0, x1);
-                f2_unpack(AY[r], y0, y1);
-                f2_unpack(AZ[r], z0, z1);
-                float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
-                if (!isfinite(fx + fy + fz)) {
-                    float xs, ys, zs, xl, yl, zl, dummy;
-                    f2_unpack(X[r], xs, dummy);
-                    f2_unpack(Y[r], ys, dummy);
-                    f2_unpack(Z[r], zs, dummy);
-                    f2_unpack(XL[r], xl, dummy);
-                    f2_unpack(YL[r], yl, dummy);
-                    f2_unpack(ZL[r], zl, dummy);
-                    const float3 f = tile_safe1_interleaved<TILE, WEIGHTED, SPLITPOS>(
-                        reinterpret_cast<const float *>(tile), reinterpret_cast<const float *>(tlo),
-                        xs, ys, zs, xl, yl, zl, p.eps2f);
-                    fx = f.x;
-                    fy = f.y;
-                    fz = f.z;
-                }
+                const float3 f = tile_partial<TILE, WEIGHTED, SPLITPOS>(
+                    AX[r], AY[r], AZ[r], tile, tlo, X[r], Y[r], Z[r], XL[r], YL[r], ZL[r], p.eps2f);
+                const float fx = f.x, fy = f.y, fz = f.z;
                 if (SMEM_ACC) {
                     sacc[r * T + tid] += (double)fx;
                     sacc[BI + r * T + tid] += (double)fy;
@@ -1088,47 +1114,14 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_cluster_kernel(const Forc
     const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
         p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int) {
             f2_t AX[R], AY[R], AZ[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
-#pragma unroll 2
-            for (int k = 0; k < TILE / 2; ++k) {
-                const float4 a = tile[2 * k];
-                const float4 b = tile[2 * k + 1];
-                const f2_t XJ = f2_pack(a.x, a.y), YJ = f2_pack(a.z, a.w), ZJ = f2_pack(b.x, b.y);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const f2_t DX = f2_sub(X[r], XJ);
-                    const f2_t DY = f2_sub(Y[r], YJ);
-                    const f2_t DZ = f2_sub(Z[r], ZJ);
-                    const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
-                    float s0, s1;
-                    f2_unpack(S, s0, s1);
-                    const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
-                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
-                    AX[r] = f2_fma(INV3, DX, AX[r]);
-                    AY[r] = f2_fma(INV3, DY, AY[r]);
-                    AZ[r] = f2_fma(INV3, DZ, AZ[r]);
-                }
-            }
+            tile_packed<R, TILE, false, false, 2>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX, AY,
+                                                  AZ);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float x0, x1, y0, y1, z0, z1;
-                f2_unpack(AX[r], x0, x1);
-                f2_unpack(AY[r], y0, y1);
-                f2_unpack(AZ[r], z0, z1);
-                float fx = x0 + x1, fy = y0 + y1, fz = z0 + z1;
-                if (!isfinite(fx + fy + fz)) {
-                    float xs, ys, zs, dummy;
-                    f2_unpack(X[r], xs, dummy);
-                    f2_unpack(Y[r], ys, dummy);
-                    f2_unpack(Z[r], zs, dummy);
-                    const float3 f = tile_safe1_interleaved<TILE>(
-                        reinterpret_cast<const float *>(tile), nullptr, xs, ys, zs, 0.f, 0.f, 0.f,
-                        p.eps2f);
-                    fx = f.x;
-                    fy = f.y;
-                    fz = f.z;
-                }
+                const float3 f = tile_partial<TILE, false, false>(
+                    AX[r], AY[r], AZ[r], tile, nullptr, X[r], Y[r], Z[r], X[r], Y[r], Z[r],
+                    p.eps2f);
+                const float fx = f.x, fy = f.y, fz = f.z;
                 sacc[r * T + tid] += (double)fx;
                 sacc[BI + r * T + tid] += (double)fy;
                 sacc[2 * BI + r * T + tid] += (double)fz;
