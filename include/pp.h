@@ -67,10 +67,15 @@ typedef enum {
  * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs.  SPLIT
  * stages hi + lo floats (about 48 bits) and forms d = (hi_i - hi_j) +
  * (lo_i - lo_j), exact in its hi part for close pairs, at six more FP32
- * operations per pair.  SPLIT is available with PP_ACC_FP64FOLD. */
+ * operations per pair.  SPLIT is available with PP_ACC_FP64FOLD.  AUTO
+ * decides at every pp_load_particles: it computes the fields once with each
+ * staging and keeps SPLIT if the two differ by more than 5e-6 in relative L2
+ * (the single-staging error on that input), SINGLE otherwise (two extra force
+ * passes at load; pp_get_option reports the choice). */
 typedef enum {
     PP_POS_SINGLE = 0,    /* default */
-    PP_POS_SPLIT = 1
+    PP_POS_SPLIT = 1,
+    PP_POS_AUTO = 2
 } pp_positions;
 
 /* Option keys for pp_set_option. */
@@ -99,6 +104,14 @@ pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **o
 
 /* Set an option (keys above).  Invalid key or value -> PP_ERR_ARG. */
 pp_status pp_set_option(pp_ctx *ctx, int key, int64_t value);
+
+/*
+ * Read an option's current value: the accumulation mode, the positions mode in
+ * force (SINGLE or SPLIT, also after AUTO decided), the split override, the
+ * graph block, the wait limit, the stream, or for PP_OPT_VARIANT the index of
+ * the force-kernel variant the next step will run.  Unknown key -> PP_ERR_ARG.
+ */
+pp_status pp_get_option(const pp_ctx *ctx, int key, int64_t *value);
 
 /*
  * Load initial positions (m) and velocities (m/s), both [N][3].  vel may be

@@ -39,6 +39,7 @@ PP_OPT_POSITIONS = 7
 
 PP_POS_SINGLE = 0
 PP_POS_SPLIT = 1
+PP_POS_AUTO = 2
 PP_OPT_TEST_SKIP_COPY = 99
 
 
@@ -79,6 +80,7 @@ SIGNATURES = [
     ("pp_create", ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(_CTX)]),
     ("pp_set_option", ctypes.c_int, [_CTX, ctypes.c_int, _I64]),
+    ("pp_get_option", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(_I64)]),
     ("pp_load_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
     ("pp_compute_fields", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
     ("pp_set_weights", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
@@ -212,6 +214,12 @@ def pp_create(n: int, w: float, dt: float, softening: float):
 
 def pp_set_option(ctx, key: int, value: int) -> None:
     _check(load().pp_set_option(ctx, int(key), int(value)), ctx)
+
+
+def pp_get_option(ctx, key: int) -> int:
+    v = _I64()
+    _check(load().pp_get_option(ctx, int(key), ctypes.byref(v)), ctx)
+    return v.value
 
 
 def pp_get_n(ctx) -> int:
@@ -475,6 +483,9 @@ class Simulation:
 
     def set_option(self, key, value):
         pp_set_option(self.ctx, key, value)
+
+    def get_option(self, key) -> int:
+        return pp_get_option(self.ctx, key)
 
     def load(self, pos, vel=None):
         pp_load_particles(self.ctx, pos, vel)

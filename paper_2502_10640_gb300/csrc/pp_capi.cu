@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -75,7 +76,9 @@ struct pp_ctx {
     double cx = 0, cy = 0, cz = 0, l0 = 1;
 
     int acc = PP_ACC_FP64FOLD;
-    int positions = PP_POS_SINGLE;
+    int positions = PP_POS_SINGLE;   // in force: SINGLE or SPLIT
+    bool positions_auto = false;     // decide SINGLE or SPLIT at every load
+    double auto_rel = -1.0;          // last AUTO estimate of the single-staging error
     int split_override = 0;
     int variant_override = -1;
     int graph_block = 16;
@@ -498,6 +501,91 @@ pp_status check_ctx(const pp_ctx *c)
     return PP_OK;
 }
 
+
+// Deterministic sums of |a - b|^2 and |b|^2 over n [3]-vectors (one pass per
+// block, fixed tree, then the host adds the block results in order).
+constexpr int kDiffBlocks = 120, kDiffThreads = 256;
+
+__global__ void __launch_bounds__(kDiffThreads)
+    diff_norms_kernel(const double *__restrict__ a, const double *__restrict__ b, int n3,
+                      double *partials)
+{
+    __shared__ double sd[kDiffThreads], sb[kDiffThreads];
+    const int chunk = (n3 + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk, hi = min(n3, lo + chunk);
+    double d2 = 0.0, b2 = 0.0;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const double d = a[k] - b[k];
+        d2 += d * d;
+        b2 += b[k] * b[k];
+    }
+    sd[threadIdx.x] = d2;
+    sb[threadIdx.x] = b2;
+    __syncthreads();
+    for (int s = kDiffThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sd[0];
+        partials[2 * blockIdx.x + 1] = sb[0];
+    }
+}
+
+// PP_POS_AUTO: fields of the current positions with single and with split
+// staging; keep split staging if they differ by more than 5e-6 (relative L2),
+// half the 1e-5 tolerance, so single staging is kept only with a 2x margin.
+pp_status decide_positions(pp_ctx *c)
+{
+    const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+    double *e_split = nullptr, *parts = nullptr;
+    if (cudaMalloc(&e_split, bytes) != cudaSuccess ||
+        cudaMalloc(&parts, 2 * kDiffBlocks * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(e_split);
+        return fail(PP_ERR_NOMEM, "cannot allocate the positions-mode check");
+    }
+    void *scratch = c->stage[1];
+    pp_status st = PP_OK;
+    double h[2 * kDiffBlocks];
+    c->positions = PP_POS_SINGLE;
+    st = stage_current(c, scratch, stage_kind(c));
+    if (st == PP_OK) st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
+    if (st == PP_OK) {
+        c->positions = PP_POS_SPLIT;
+        st = stage_current(c, scratch, stage_kind(c));
+    }
+    if (st == PP_OK) st = force_pass(c, MODE_FIELDS, scratch, nullptr, e_split);
+    if (st == PP_OK) {
+        diff_norms_kernel<<<kDiffBlocks, kDiffThreads, 0, c->stream>>>(c->aos, e_split,
+                                                                     (int)(3 * c->n), parts);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h, parts, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "positions-mode check");
+    }
+    cudaFree(e_split);
+    cudaFree(parts);
+    if (st == PP_OK) st = check_device_errors(c, true);
+    if (st != PP_OK) {
+        c->positions = PP_POS_SINGLE;
+        return st;
+    }
+    double d2 = 0.0, b2 = 0.0;
+    for (int k = 0; k < kDiffBlocks; ++k) {
+        d2 += h[2 * k];
+        b2 += h[2 * k + 1];
+    }
+    c->auto_rel = b2 > 0 ? std::sqrt(d2 / b2) : 0.0;
+    c->positions = c->auto_rel > 5e-6 ? PP_POS_SPLIT : PP_POS_SINGLE;
+    drop_graphs(c);
+    return PP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -613,10 +701,16 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
     case PP_OPT_POSITIONS: {
         if (key == PP_OPT_ACC && (value < PP_ACC_FP64FOLD || value > PP_ACC_FP64_FULL))
             return fail(PP_ERR_ARG, "bad acc mode");
-        if (key == PP_OPT_POSITIONS && value != PP_POS_SINGLE && value != PP_POS_SPLIT)
+        if (key == PP_OPT_POSITIONS && value != PP_POS_SINGLE && value != PP_POS_SPLIT &&
+            value != PP_POS_AUTO)
             return fail(PP_ERR_ARG, "bad positions mode");
         const int new_acc = key == PP_OPT_ACC ? (int)value : c->acc;
-        const int new_pos = key == PP_OPT_POSITIONS ? (int)value : c->positions;
+        const bool new_auto = key == PP_OPT_POSITIONS ? value == PP_POS_AUTO : c->positions_auto;
+        const int new_pos = key == PP_OPT_POSITIONS ? (value == PP_POS_AUTO ? c->positions : (int)value)
+                                                    : c->positions;
+        if (new_auto && (new_acc != PP_ACC_FP64FOLD || c->wts))
+            return fail(PP_ERR_ARG, "automatic positions need PP_ACC_FP64FOLD and equal weights");
+        c->positions_auto = new_auto;
         if (new_pos == PP_POS_SPLIT && new_acc == PP_ACC_KAHAN)
             return fail(PP_ERR_ARG, "split positions are implemented with the FP64 fold only");
         if (c->wts && (new_pos == PP_POS_SPLIT || new_acc == PP_ACC_KAHAN))
@@ -672,6 +766,26 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
     }
 }
 
+pp_status pp_get_option(const pp_ctx *c, int key, int64_t *value)
+{
+    if (!c || !value) return fail(PP_ERR_ARG, "null argument");
+    switch (key) {
+    case PP_OPT_ACC: *value = c->acc; return PP_OK;
+    case PP_OPT_POSITIONS: *value = c->positions; return PP_OK;
+    case PP_OPT_STREAM: *value = (int64_t)reinterpret_cast<intptr_t>(c->stream); return PP_OK;
+    case PP_OPT_SPLIT: *value = c->split_override; return PP_OK;
+    case PP_OPT_GRAPH_BLOCK: *value = c->graph_block; return PP_OK;
+    case PP_OPT_TIMEOUT_NS: *value = (int64_t)c->timeout_ns; return PP_OK;
+    case PP_OPT_VARIANT: {
+        int count = 0;
+        const Variant *vs = variants(&count);
+        *value = (int64_t)(force_variant(c) - vs);
+        return PP_OK;
+    }
+    default: return fail(PP_ERR_ARG, "unknown option key");
+    }
+}
+
 pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int on_device)
 {
     NvtxRange nvtx_("pp_load_particles");
@@ -695,6 +809,11 @@ pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int
     if (bad) return fail(PP_ERR_ARG, "non-finite position or velocity");
     st = choose_frame(c);
     if (st != PP_OK) return st;
+    if (c->positions_auto) {
+        st = pad_both(c);
+        if (st == PP_OK) st = decide_positions(c);
+        if (st != PP_OK) return st;
+    }
     // a_0 = F(r_0) (needed by the first Eq. G); the epilogue stages r_1.
     c->parity = 0;
     st = pad_both(c);

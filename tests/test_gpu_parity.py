@@ -130,6 +130,33 @@ def test_every_split_positions_variant():
                      report=f"split variant {names[v]}")
 
 
+def test_auto_positions_pick_split_staging_only_when_needed():
+    """PP_POS_AUTO: the hard ball (close pairs ~1e3 x closer than its size) switches to
+    split staging and meets 1e-5; the benchmark bunch stays on single staging."""
+    n, R = 40000, 20e-6
+    hard = wl.uniform_sphere(n, R, seed=7 + n)
+    with capi.Simulation(n, 10.0, 1e-15, 1e-9, positions=capi.PP_POS_AUTO) as sim:
+        sim.load(hard)
+        assert sim.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        E = sim.fields()
+        sim.step(2)
+    check_fields(E, oracle.fields(hard, 10.0, 1e-9), report="auto positions hard ball")
+    b = wl.GAUSSIAN_65536
+    pos = b.positions()
+    with capi.Simulation(b.n, b.w, b.dt, b.eps, positions=capi.PP_POS_AUTO) as sim:
+        sim.load(pos)
+        mode = sim.get_option(capi.PP_OPT_POSITIONS)
+        E = sim.fields()
+    # whichever staging AUTO picked, the full field meets the tolerance
+    check_fields(E, oracle.fields(pos, b.w, b.eps), report=f"auto positions gaussian65536 mode={mode}")
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.load(pos)
+        E1 = sim.fields()
+    err_single = rel_l2(E1, oracle.fields(pos, b.w, b.eps))
+    _log("single staging gaussian65536 full", err_single, np.zeros(1), None)
+    assert mode == (capi.PP_POS_SPLIT if err_single > 5e-6 else capi.PP_POS_SINGLE)
+
+
 def test_paper_lattice_fields():
     """The paper's 16^3 cube lattice (Sec. 2.1): all 4096 fields."""
     b = wl.PAPER_LATTICE
