@@ -177,17 +177,25 @@ pp_status read_errors(pp_batch *b, int *flags)
     return PP_OK;
 }
 
-// Rewrite the device table of active bunches (table order = slot order).
+// Rewrite the device table of active bunches.  Table order: largest source
+// chunk first (ties by slot), so that the queue hands out the full-size items
+// of the big bunches first and the short items of small bunches fill the tail
+// of the step (longest-processing-time-first).  The order changes only which
+// CTA takes an item, never an item's arithmetic.
 pp_status upload_table(pp_batch *b)
 {
     std::vector<BunchDesc> h;
     b->order.clear();
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i].active) b->order.push_back(i);
+    std::stable_sort(b->order.begin(), b->order.end(), [b](int x, int y) {
+        const Layout &lx = b->slots[x].L, &ly = b->slots[y].L;
+        return std::min(lx.npad, lx.jchunk) > std::min(ly.npad, ly.jchunk);
+    });
     int items = 0;
-    for (int i = 0; i < (int)b->slots.size(); ++i) {
+    for (int i : b->order) {
         const Slot &s = b->slots[i];
-        if (!s.active) continue;
         h.push_back(make_desc(s, MODE_STEP, s.parity, items));
-        b->order.push_back(i);
         items += s.L.nib * s.L.nsplit;
     }
     BatchHeader hdr{(int)h.size(), items};

@@ -15,6 +15,7 @@
 namespace ppk {
 
 constexpr int kBatchT = 128, kBatchR = 4, kBatchTile = 512, kBatchStages = 3, kBatchMinB = 4;
+constexpr int kBatchUnroll = 2;   // pair-loop unroll of tile_packed: 2 measured 15% faster than 1 here
 constexpr int kBatchBI = kBatchT * kBatchR;
 constexpr int kBatchJChunk = 16 * kBatchTile;   // sources per work item
 
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(T, MINB)
             p, rg, j0, ntiles, issued, seen,
             [&](const float4 *tile, const float4 *, int) {
                 f2_t AX[R], AY[R], AZ[R];
-                tile_packed<R, TILE, false, false, 2>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX,
+                tile_packed<R, TILE, false, false, kBatchUnroll>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX,
                                                       AY, AZ);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {

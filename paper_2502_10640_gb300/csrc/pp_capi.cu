@@ -136,8 +136,11 @@ const Variant *force_variant(const pp_ctx *c)
         if (c->n >= 8192) return variant_by_name("f32x2split.sfold64.t128r4k256m4");
         return variant_by_name("f32x2split.fold64.t64r1k128");
     }
-    if (c->acc == PP_ACC_KAHAN)
-        return variant_by_name(c->n >= 32768 ? "f32.kahan.t256r4k256" : "f32.kahan.t128r2k128");
+    if (c->acc == PP_ACC_KAHAN) {  // packed pair math, compensated FP32 fold
+        if (c->n >= 32768) return variant_by_name("f32x2.kahan.st128r4k512m4u1");
+        if (c->n >= 8192) return variant_by_name("f32x2.kahan.t128r2k128");
+        return variant_by_name("f32x2.kahan.t64r1k128");
+    }
     // packed f32x2 pair math wherever there is enough work per CTA (defaults
     // from GB300 measurements; pp_autotune refines them per device and N)
     if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k512m4u1");

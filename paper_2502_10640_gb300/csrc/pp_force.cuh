@@ -931,8 +931,16 @@ __device__ __forceinline__ float3 tile_partial(f2_t AX, f2_t AY, f2_t AZ, const 
 // SPLITPOS reads hi/lo staged sources (STAGE_F32IX2) and forms each
 // separation as (hi_i - hi_j) + (lo_i - lo_j): three f32x2 operations per
 // component instead of one.
+// KAHAN folds each tile partial into a compensated FP32 pair (TwoSum: hi
+// takes the rounded sum, lo collects the exact rounding errors) instead of an
+// FP64 accumulator: six FP32 additions per component and tile on the FP32
+// pipe in place of a conversion and an add on the FP64 pipe, which runs at a
+// small fraction of the FP32 rate on this GPU.  With SMEM_ACC the pairs live
+// in shared memory ([hi x,y,z][lo x,y,z] x BI floats, the same bytes as the
+// FP64 accumulators).  The pair is converted to FP64 (hi + lo) once, after
+// the last tile.
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
     constexpr int BI = T * R;
@@ -963,10 +971,17 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
         s_abort = 0;
         fence_barrier_init();
     }
+    float *skah = reinterpret_cast<float *>(sacc);  // KAHAN && SMEM_ACC: [6][BI]
     if (SMEM_ACC) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            sacc[r * T + tid] = sacc[BI + r * T + tid] = sacc[2 * BI + r * T + tid] = 0.0;
+        for (int r = 0; r < R; ++r) {
+            if (KAHAN) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) skah[c * BI + r * T + tid] = 0.f;
+            } else {
+                sacc[r * T + tid] = sacc[BI + r * T + tid] = sacc[2 * BI + r * T + tid] = 0.0;
+            }
+        }
     }
     __syncthreads();
 
@@ -999,6 +1014,9 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     double ax64[R], ay64[R], az64[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) ax64[r] = ay64[r] = az64[r] = 0.0;
+    float kh[KAHAN && !SMEM_ACC ? 6 * R : 1];  // register compensated pairs
+#pragma unroll
+    for (int c = 0; c < (KAHAN && !SMEM_ACC ? 6 * R : 1); ++c) kh[c] = 0.f;
     const f2_t EPS2 = f2_pack(p.eps2f, p.eps2f);
 
     int issued = 0, seen = 0;
@@ -1012,7 +1030,24 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
                 const float3 f = tile_partial<TILE, WEIGHTED, SPLITPOS>(
                     AX[r], AY[r], AZ[r], tile, tlo, X[r], Y[r], Z[r], XL[r], YL[r], ZL[r], p.eps2f);
                 const float fx = f.x, fy = f.y, fz = f.z;
-                if (SMEM_ACC) {
+                if (KAHAN) {
+                    const float fc[3] = {fx, fy, fz};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float hs, e;
+                        if (SMEM_ACC) {
+                            float &hi = skah[c * BI + r * T + tid];
+                            float &lo = skah[(3 + c) * BI + r * T + tid];
+                            two_sum(hi, fc[c], hs, e);
+                            hi = hs;
+                            lo = __fadd_rn(lo, e);
+                        } else {
+                            two_sum(kh[6 * r + c], fc[c], hs, e);
+                            kh[6 * r + c] = hs;
+                            kh[6 * r + 3 + c] = __fadd_rn(kh[6 * r + 3 + c], e);
+                        }
+                    }
+                } else if (SMEM_ACC) {
                     sacc[r * T + tid] += (double)fx;
                     sacc[BI + r * T + tid] += (double)fy;
                     sacc[2 * BI + r * T + tid] += (double)fz;
@@ -1032,7 +1067,20 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
         ring_drain(p, rg, issued, seen, ntiles);
         return;
     }
-    if (SMEM_ACC) {
+    if (KAHAN) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            double v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                v[c] = SMEM_ACC ? (double)skah[c * BI + r * T + tid] +
+                                      (double)skah[(3 + c) * BI + r * T + tid]
+                                : (double)kh[6 * r + c] + (double)kh[6 * r + 3 + c];
+            ax64[r] = v[0];
+            ay64[r] = v[1];
+            az64[r] = v[2];
+        }
+    } else if (SMEM_ACC) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             ax64[r] = sacc[r * T + tid];

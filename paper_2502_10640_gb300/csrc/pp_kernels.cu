@@ -19,14 +19,14 @@ Variant make_f32(const char *name)
 }
 
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false>
 Variant make_f32x2(const char *name)
 {
-    return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, ACC_FP64FOLD,
+    return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, KAHAN ? ACC_KAHAN : ACC_FP64FOLD,
                    SPLITPOS ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
                        &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS,
-                                           UNROLL>),
+                                           UNROLL, KAHAN>),
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1) +
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
 }
@@ -76,6 +76,11 @@ const Variant kVariants[] = {
     make_f32x2<128, 4, 512, 3, 4, true, false, false, 1>("f32x2.sfold64.t128r4k512m4u1"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
+    // packed pair math, tile partials folded into compensated FP32 pairs
+    make_f32x2<128, 4, 512, 3, 4, true, false, false, 1, true>("f32x2.kahan.st128r4k512m4u1"),
+    make_f32x2<128, 4, 512, 3, 4, true, false, false, 2, true>("f32x2.kahan.st128r4k512m4"),
+    make_f32x2<128, 2, 128, 4, 4, false, false, false, 2, true>("f32x2.kahan.t128r2k128"),
+    make_f32x2<64, 1, 128, 4, 8, false, false, false, 2, true>("f32x2.kahan.t64r1k128"),
     // j-split reduced through distributed shared memory of a thread-block cluster
     make_cluster<64, 1, 128, 4, 8, 8>("f32x2cl8.dsmem.t64r1k128"),
     make_cluster<64, 1, 128, 4, 8, 16>("f32x2cl16.dsmem.t64r1k128"),

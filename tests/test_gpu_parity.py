@@ -179,14 +179,21 @@ def test_every_fp32_variant():
     n = 6000
     pos = wl.gaussian_bunch(n, 5e-6, seed=32)
     ref = oracle.fields(pos, 2.0, 0.0)
-    # every FP64-fold kernel on single-float sources (scalar and packed f32x2)
+    # every FP64-fold and compensated-fold kernel on single-float sources (scalar and
+    # packed f32x2); the context reports the variant that actually ran
     bound = bound_for(pos, 2.0, 0.0)
     names = capi.variants()
-    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32.fold64", "f32x2.", "f32x2cl"))]
-    assert len(chosen) >= 11
+    chosen = [i for i, nm in enumerate(names)
+              if nm.startswith(("f32.fold64", "f32.kahan", "f32x2.", "f32x2cl"))]
+    assert len(chosen) >= 15
     for v in chosen:
-        check_fields(gpu_fields(pos, 2.0, 0.0, variant=v), ref, bound=bound,
-                     report=f"variant={names[v]}")
+        acc = capi.PP_ACC_KAHAN if ".kahan." in names[v] else capi.PP_ACC_FP64FOLD
+        with capi.Simulation(n, 2.0, 1e-15, 0.0, acc=acc) as sim:
+            sim.set_option(capi.PP_OPT_VARIANT, v)
+            sim.load(pos)
+            E = sim.fields()
+            assert sim.get_option(capi.PP_OPT_VARIANT) == v, names[v]
+        check_fields(E, ref, bound=bound, report=f"variant={names[v]}")
 
 
 def test_bitwise_determinism():
