@@ -143,7 +143,7 @@ const Variant *force_variant(const pp_ctx *c)
     }
     // packed f32x2 pair math wherever there is enough work per CTA (defaults
     // from GB300 measurements; pp_autotune refines them per device and N)
-    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k512m4u1");
+    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k1024s2m4u1");
     if (c->n >= 8192) return variant_by_name("f32x2.fold64.t128r2k128");
     return variant_by_name("f32x2.fold64.t64r1k128");
 }

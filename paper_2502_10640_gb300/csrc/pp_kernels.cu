@@ -74,6 +74,7 @@ const Variant kVariants[] = {
     make_f32x2<128, 4, 512, 3, 5, true>("f32x2.sfold64.t128r4k512m5"),
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
     make_f32x2<128, 4, 512, 3, 4, true, false, false, 1>("f32x2.sfold64.t128r4k512m4u1"),
+    make_f32x2<128, 4, 1024, 2, 4, true, false, false, 1>("f32x2.sfold64.t128r4k1024s2m4u1"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
     // packed pair math, tile partials folded into compensated FP32 pairs
