@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", default=None,
+                    help="run this force-kernel variant (by name) instead of autotuning")
+    ap.add_argument("--split", type=int, default=0,
+                    help="with --variant: j-split override (0 = the library's plan)")
     ap.add_argument("--batch-steps", type=int, default=8,
                     help="steps of the 64-bunch mix, batched and one bunch per launch (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=32,
@@ -87,25 +91,26 @@ def load_peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per force launch from the committed ncu summary, or None once the
-    kernel sources differ from the ones that capture was taken on."""
-    import glob
+def profiled_traffic(variant: str, split: int):
+    """DRAM bytes per force launch of this plan (kernel variant, j-split override) from the
+    committed ncu record, or None if no capture of this plan exists or the kernel sources
+    differ from the ones the captures were taken on."""
     import hashlib
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.json"))):
+    path = os.path.join(ROOT, "profiles", "force_f32x2_gaussian65536_traffic.json")
+    try:
         with open(path) as f:
             rec = json.load(f)
-        if "gaussian65536" not in os.path.basename(path):
-            continue
         h = hashlib.sha256()
-        try:
-            for src in rec["sources"]:
-                with open(os.path.join(ROOT, src), "rb") as f:
-                    h.update(f.read())
-        except OSError:
-            return None
-        if h.hexdigest() == rec["sources_sha256"]:
-            return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    for r in rec["records"]:
+        if r["variant"] == variant and int(r["split"]) == int(split):
+            return r["dram_bytes_read_per_launch"] + r["dram_bytes_write_per_launch"]
     return None
 
 
@@ -354,7 +359,14 @@ def run_ours(args):
     sim = capi.Simulation(n, b.w, b.dt, b.eps)
     sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
     sim.load(pos0)
-    tune = None if args.no_autotune else sim.autotune()     # set-up, not timed
+    if args.variant:
+        sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index(args.variant))
+        sim.set_option(capi.PP_OPT_SPLIT, args.split)
+        tune = None
+    else:
+        tune = None if args.no_autotune else sim.autotune()     # set-up, not timed
+    plan_variant = capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)]
+    plan_split = sim.get_option(capi.PP_OPT_SPLIT)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize(dev)
@@ -383,23 +395,36 @@ def run_ours(args):
     # end to end through the public API with pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
+        # pinned host buffers: as torch tensors the binding passes them as
+        # PP_MEM_HOST_MAPPED (the kernels read and write them over the CPU-GPU link);
+        # as numpy views of the same memory, as PP_MEM_HOST (copy engine + scratch)
         pin = [torch.empty((n, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
         hp, hv, ha = (x.numpy() for x in pin)
         p, v, a, step, frame = sim.state()
         hp[:], hv[:], ha[:] = p, v, a
-        t_e2e = 0.0
-        for k in range(args.e2e_steps):
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            sim.set_state(hp, hv, ha, step, frame)
-            sim.step(1)
-            capi.pp_get_state(sim.ctx, hp, hv, ha)
-            t_e2e += time.perf_counter() - t0
-            step += 1
-        t_e2e = max_over_ranks(t_e2e)
-        e2e = {"value": float(n) * n * args.e2e_steps * world / t_e2e / 1e9, "unit": UNIT,
+
+        def e2e_run(bufs):
+            nonlocal step
+            t = 0.0
+            for k in range(args.e2e_steps):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                sim.set_state(*bufs, step, frame)
+                sim.step(1)
+                capi.pp_get_state(sim.ctx, *bufs)
+                t += time.perf_counter() - t0
+                step += 1
+            return max_over_ranks(t)
+
+        t_copy = e2e_run((hp, hv, ha))
+        t_e2e = e2e_run(pin)
+        rate = lambda t: float(n) * n * args.e2e_steps * world / t / 1e9
+        e2e = {"value": rate(t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 3 * n * 3 * 8,
-               "api": "pp_set_state(host r,v,a) + pp_step(1) + pp_get_state(host r,v,a)"}
+               "api": "pp_set_state(pinned host r,v,a) + pp_step(1) + pp_get_state(pinned host "
+                      "r,v,a), PP_MEM_HOST_MAPPED",
+               "copy_engine_value": rate(t_copy),
+               "copy_engine_api": "the same calls with PP_MEM_HOST (copy engine through scratch)"}
 
     sim.close()
     batched = run_batched(args.batch_steps) if (args.batch_steps > 0 and world == 1) else None
@@ -429,11 +454,11 @@ def run_ours(args):
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "pct_fp32_peak": 100.0 * achieved / peak,
-                   "kernel": (tune or {}).get("variant_name", "default plan"),
-                   "split": (tune or {}).get("split"),
+                   "kernel": plan_variant,
+                   "split": plan_split,
                    "autotuned": tune is not None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "frac": achieved / peak, "traffic": profiled_traffic(plan_variant, plan_split),
                      "note": f"{FLOP_PER_PAIR} flop per pair; peak = 2 x 128 FP32 lanes x {sms} SMs x "
                              f"{max_mhz:.0f} MHz ({'sm_max_mhz of measured peaks file' if peak_src == 'measured' else 'fallback clock'})"},
         "gpu_launches": args.steps,

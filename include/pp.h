@@ -24,10 +24,20 @@
  *   - pp_last_error() gives a message for the last non-OK status returned
  *     on the calling thread.
  *   - Array arguments are [N][3] row-major doubles (x, y, z of particle i
- *     at 3i, 3i+1, 3i+2).  on_device = 0: host memory (pageable or pinned);
- *     on_device = 1: device memory of the context's GPU, read or written in
- *     order on the context's stream.  Inputs are copied; the caller keeps
- *     ownership of every buffer it passes.
+ *     at 3i, 3i+1, 3i+2).  The on_device argument says where they live
+ *     (enum pp_mem): PP_MEM_HOST (0), host memory, pageable or page-locked,
+ *     moved by the copy engine through library scratch; PP_MEM_DEVICE (1),
+ *     device memory of the context's GPU, read or written in order on the
+ *     context's stream; PP_MEM_HOST_MAPPED (2), page-locked host memory that
+ *     CUDA maps into the device address space (cudaHostAlloc, cudaMallocHost,
+ *     cudaHostRegister, pinned PyTorch tensors), read or written directly by
+ *     the library's kernels over the CPU-GPU link with no staging copy.  For
+ *     PP_MEM_HOST_MAPPED the whole [N][3] array must lie in one such
+ *     allocation; the library checks this on the host before any kernel
+ *     touches the buffer and returns PP_ERR_ARG otherwise (pageable memory
+ *     included).  The batch calls accept all three kinds and move mapped
+ *     memory like PP_MEM_HOST.  Any other value: PP_ERR_ARG.  Inputs are
+ *     copied; the caller keeps ownership of every buffer it passes.
  *   - The library owns all device memory it allocates; pp_destroy frees it.
  *   - Calls on one context must not run concurrently from several threads.
  *   - Calls return after the work they enqueue has finished (the stream is
@@ -44,6 +54,13 @@ extern "C" {
 #endif
 
 typedef struct pp_ctx pp_ctx;
+
+/* Where a caller's array lives (the on_device argument of the calls below). */
+typedef enum {
+    PP_MEM_HOST = 0,         /* host memory, through the copy engine */
+    PP_MEM_DEVICE = 1,       /* device memory of the context's GPU */
+    PP_MEM_HOST_MAPPED = 2   /* mapped page-locked host memory, accessed by the kernels */
+} pp_mem;
 
 typedef enum {
     PP_OK = 0,
@@ -188,6 +205,16 @@ pp_status pp_get_state(pp_ctx *ctx, double *pos, double *vel, double *acc, int64
                        double *frame, int on_device);
 pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const double *acc,
                        int64_t step, const double *frame, int on_device);
+
+/*
+ * pp_check_mapped -- the paper has no counterpart; a service call.  PP_OK if
+ * the `bytes` bytes at p may be passed as PP_MEM_HOST_MAPPED: page-locked host
+ * memory mapped into the device address space, all of it in one allocation.
+ * Otherwise PP_ERR_ARG, reason via pp_last_error(NULL).  Host-side only: no
+ * kernel runs and the device never touches p.  Every call taking a
+ * PP_MEM_HOST_MAPPED buffer makes this check before its kernels run.
+ */
+pp_status pp_check_mapped(const void *p, int64_t bytes);
 
 /*
  * pp_fields_noalloc -- the paper has no counterpart; this is a service entry

@@ -42,6 +42,10 @@ PP_POS_SPLIT = 1
 PP_POS_AUTO = 2
 PP_OPT_TEST_SKIP_COPY = 99
 
+PP_MEM_HOST = 0
+PP_MEM_DEVICE = 1
+PP_MEM_HOST_MAPPED = 2
+
 
 class PPError(RuntimeError):
     def __init__(self, status: int, message: str):
@@ -82,6 +86,7 @@ SIGNATURES = [
     ("pp_set_option", ctypes.c_int, [_CTX, ctypes.c_int, _I64]),
     ("pp_get_option", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(_I64)]),
     ("pp_load_particles", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int]),
+    ("pp_check_mapped", ctypes.c_int, [ctypes.c_void_p, _I64]),
     ("pp_compute_fields", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
     ("pp_set_weights", ctypes.c_int, [_CTX, _DP, ctypes.c_int]),
     ("pp_step", ctypes.c_int, [_CTX, _I64]),
@@ -150,12 +155,17 @@ def _is_torch(x) -> bool:
 
 
 def _arg(x, n: int | None, writable: bool):
-    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor."""
+    """(pointer, memory kind, keepalive) for a numpy array or a torch tensor: CUDA tensors
+    are PP_MEM_DEVICE, pinned CPU tensors (contiguous float64 of the right shape)
+    PP_MEM_HOST_MAPPED, everything else PP_MEM_HOST."""
     if x is None:
-        return None, 0, None
+        return None, PP_MEM_HOST, None
     if _is_torch(x):
         import torch
         if not x.is_cuda:
+            if (x.is_pinned() and x.dtype == torch.float64 and x.is_contiguous()
+                    and (n is None or tuple(x.shape) == (n, 3))):
+                return x.data_ptr(), PP_MEM_HOST_MAPPED, x
             x = x.numpy()
         else:
             if x.dtype != torch.float64 or not x.is_contiguous():
@@ -165,7 +175,7 @@ def _arg(x, n: int | None, writable: bool):
             if n is not None and tuple(x.shape) not in ((n, 3),):
                 raise ValueError(f"expected shape ({n}, 3), got {tuple(x.shape)}")
             torch.cuda.current_stream(x.device).synchronize()
-            return x.data_ptr(), 1, x
+            return x.data_ptr(), PP_MEM_DEVICE, x
     a = x
     if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
         if writable:
@@ -173,7 +183,7 @@ def _arg(x, n: int | None, writable: bool):
         a = np.ascontiguousarray(a, dtype=np.float64)
     if n is not None and a.shape != (n, 3):
         raise ValueError(f"expected shape ({n}, 3), got {a.shape}")
-    return a.ctypes.data, 0, a
+    return a.ctypes.data, PP_MEM_HOST, a
 
 
 def _same_kind(*ons):
@@ -311,6 +321,12 @@ def pp_set_state(ctx, pos, vel, acc, step: int, frame=None) -> None:
     on = _same_kind(op, ov, oa)
     fr = None if frame is None else (ctypes.c_double * 4)(*[float(x) for x in frame])
     _check(load().pp_set_state(ctx, p, v, a, int(step), fr, on), ctx)
+
+
+def pp_check_mapped(ptr: int, nbytes: int) -> None:
+    """Raise PPError unless the nbytes at address ptr may be passed as PP_MEM_HOST_MAPPED
+    (host-side check only; nothing runs on the device)."""
+    _check(load().pp_check_mapped(ctypes.c_void_p(int(ptr)), int(nbytes)))
 
 
 def pp_autotune(ctx) -> dict:

@@ -420,6 +420,8 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
 {
     NvtxRange nvtx_("pp_batch_add");
     if (!b || !pos || !slot_out) return bfail(PP_ERR_ARG, "null argument");
+    if (on_device < PP_MEM_HOST || on_device > PP_MEM_HOST_MAPPED)
+        return bfail(PP_ERR_ARG, "bad memory kind");
     if (N < 1 || N > (int64_t(1) << 28)) return bfail(PP_ERR_ARG, "N must be in [1, 2^28]");
     if (!(std::isfinite(w) && w > 0) || !(std::isfinite(dt) && dt > 0) ||
         !(std::isfinite(softening) && softening >= 0))
@@ -482,7 +484,7 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
         cudaMemsetAsync(s.tickets, 0, L.ticket_bytes, b->stream) != cudaSuccess)
         return undo(PP_ERR_CUDA, "memset failed");
     const double *src = pos;
-    if (!on_device) {
+    if (on_device != PP_MEM_DEVICE) {
         if (cudaMemcpyAsync(s.aos, pos, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
             return undo(PP_ERR_CUDA, "copy of positions failed");
         src = s.aos;
@@ -491,7 +493,7 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
         return undo(PP_ERR_CUDA, "layout conversion failed");
     if (vel) {
         const double *vs = vel;
-        if (!on_device) {
+        if (on_device != PP_MEM_DEVICE) {
             if (cudaMemcpyAsync(s.aos, vel, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
                 return undo(PP_ERR_CUDA, "copy of velocities failed");
             vs = s.aos;
@@ -600,6 +602,8 @@ pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, do
                              int64_t *step, int on_device)
 {
     if (pp_status st = check_slot(b, slot)) return st;
+    if (on_device < PP_MEM_HOST || on_device > PP_MEM_HOST_MAPPED)
+        return bfail(PP_ERR_ARG, "bad memory kind");
     B_CUDA(cudaSetDevice(b->device));
     Slot &s = b->slots[slot];
     if (s.step < 0) return bfail(PP_ERR_STATE, "bunch state is unspecified after a timeout");
@@ -608,9 +612,9 @@ pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, do
     const size_t bytes = (size_t)s.n * 3 * sizeof(double);
     for (int k = 0; k < 3; ++k) {
         if (!outs[k]) continue;
-        double *target = on_device ? outs[k] : s.aos;
+        double *target = on_device == PP_MEM_DEVICE ? outs[k] : s.aos;
         B_CUDA(launch_soa_to_aos(arrs[k][0], arrs[k][1], arrs[k][2], (int)s.n, target, b->stream));
-        if (!on_device)
+        if (on_device != PP_MEM_DEVICE)
             B_CUDA(cudaMemcpyAsync(outs[k], s.aos, bytes, cudaMemcpyDeviceToHost, b->stream));
     }
     if (step) *step = s.step;

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/pp.h"
 #include "pp_internal.h"
 
@@ -387,35 +389,123 @@ pp_status pad_both(pp_ctx *c)
 }
 
 // Stage the pending positions drift(r_n, v_n, a_n) into stage[parity].
-pp_status restage_pending(pp_ctx *c)
+pp_status restage_pending(pp_ctx *c, bool sync = true)
 {
     if (pp_status st = pad_both(c)) return st;
     PP_CUDA(launch_stage_drift(c->r, c->v, c->a, (int)c->n, c->npad, c->stage[c->parity],
                                stage_kind(c), c->dt, c->dt * c->dt / 2.0, c->cx, c->cy, c->cz,
                                1.0 / c->l0, c->stream, c->wrel));
-    PP_CUDA(cudaStreamSynchronize(c->stream));
+    if (sync) PP_CUDA(cudaStreamSynchronize(c->stream));
     return PP_OK;
 }
 
-// Copy [n][3] from the caller (host or device) into SoA dst; check finiteness.
-pp_status import_aos(pp_ctx *c, const double *src, int on_device, double *const dst[3])
+bool valid_mem(int kind) { return kind >= PP_MEM_HOST && kind <= PP_MEM_HOST_MAPPED; }
+
+// Size of the CUDA allocation holding p, from the driver's pointer attributes
+// (false where the driver does not report a range for this kind of memory).
+bool allocation_range(const void *p, uintptr_t *start, size_t *size)
+{
+    using GetAttr = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+    static GetAttr fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetAttr>(f);
+    }();
+    if (!fn) return false;
+    CUdeviceptr st = 0;
+    size_t sz = 0;
+    if (fn(&st, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS ||
+        fn(&sz, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS ||
+        sz == 0)
+        return false;
+    *start = (uintptr_t)st;
+    *size = sz;
+    return true;
+}
+
+// True if the byte at q is mapped page-locked host memory whose device-side
+// address is q - base + dbase.
+bool mapped_byte(uintptr_t q, uintptr_t base, uintptr_t dbase)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, reinterpret_cast<const void *>(q)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer &&
+           (uintptr_t)at.devicePointer == dbase + (q - base);
+}
+
+// Device-side address of a caller's PP_MEM_HOST_MAPPED buffer of `bytes`
+// bytes.  The buffer must be page-locked host memory that CUDA maps into the
+// device address space, and all of it must lie in one such allocation.  This
+// is checked on the host, before any kernel touches the buffer: its first and
+// last bytes must be mapped with contiguous device addresses, and the whole
+// range must lie inside the allocation range the driver reports; where the
+// driver reports none, every 4 KB page of the range is checked instead.
+pp_status mapped_view(const void *p, size_t bytes, const void **dptr)
+{
+    if (!p || bytes == 0) return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer is empty");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer is not CUDA page-locked host memory");
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer)
+        return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer is not mapped page-locked host memory");
+    const uintptr_t lo = (uintptr_t)p, hi = lo + bytes, dlo = (uintptr_t)at.devicePointer;
+    if (hi < lo || !mapped_byte(hi - 1, lo, dlo))
+        return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer extends past its allocation");
+    uintptr_t start = 0;
+    size_t size = 0;
+    if (allocation_range(p, &start, &size)) {
+        if (lo < start || hi > start + size)
+            return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer extends past its allocation");
+    } else {
+        for (uintptr_t q = (lo & ~(uintptr_t)4095) + 4096; q < hi; q += 4096)
+            if (!mapped_byte(q, lo, dlo))
+                return fail(PP_ERR_ARG, "PP_MEM_HOST_MAPPED buffer extends past its allocation");
+    }
+    *dptr = at.devicePointer;
+    return PP_OK;
+}
+
+// Copy [n][3] from the caller into SoA dst; check finiteness.  Host memory
+// goes through the copy engine into library scratch; device memory and mapped
+// host memory are read by the conversion kernel itself.
+pp_status import_aos(pp_ctx *c, const double *src, int kind, double *const dst[3])
 {
     const size_t bytes = (size_t)c->n * 3 * sizeof(double);
     const double *dsrc = src;
-    if (!on_device) {
+    if (kind == PP_MEM_HOST) {
         PP_CUDA(cudaMemcpyAsync(c->aos, src, bytes, cudaMemcpyHostToDevice, c->stream));
         dsrc = c->aos;
+    } else if (kind == PP_MEM_HOST_MAPPED) {
+        const void *d = nullptr;
+        if (pp_status st = mapped_view(src, bytes, &d)) return st;
+        dsrc = static_cast<const double *>(d);
     }
     PP_CUDA(launch_aos_to_soa(dsrc, (int)c->n, dst[0], dst[1], dst[2], c->err + 1, c->stream));
     return PP_OK;
 }
 
-pp_status export_aos(pp_ctx *c, double *const src[3], double *out, int on_device)
+pp_status export_aos(pp_ctx *c, double *const src[3], double *out, int kind)
 {
     const size_t bytes = (size_t)c->n * 3 * sizeof(double);
-    double *target = on_device ? out : c->aos;
+    double *target = out;
+    if (kind == PP_MEM_HOST) {
+        target = c->aos;
+    } else if (kind == PP_MEM_HOST_MAPPED) {
+        const void *d = nullptr;
+        if (pp_status st = mapped_view(out, bytes, &d)) return st;
+        target = static_cast<double *>(const_cast<void *>(d));
+    }
     PP_CUDA(launch_soa_to_aos(src[0], src[1], src[2], (int)c->n, target, c->stream));
-    if (!on_device)
+    if (kind == PP_MEM_HOST)
         PP_CUDA(cudaMemcpyAsync(out, c->aos, bytes, cudaMemcpyDeviceToHost, c->stream));
     return PP_OK;
 }
@@ -794,6 +884,7 @@ pp_status pp_load_particles(pp_ctx *c, const double *pos, const double *vel, int
     NvtxRange nvtx_("pp_load_particles");
     if (pp_status s = check_ctx(c)) return s;
     if (!pos) return fail(PP_ERR_ARG, "pos is null");
+    if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
     PP_CUDA(cudaSetDevice(c->device));
     drop_graphs(c);
     c->loaded = false;
@@ -836,6 +927,7 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
 {
     if (pp_status s = check_ctx(c)) return s;
     PP_CUDA(cudaSetDevice(c->device));
+    if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
     if (c->acc == PP_ACC_KAHAN || c->positions == PP_POS_SPLIT)
         return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL "
                                 "with single positions");
@@ -857,8 +949,9 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
             }
         }
         const size_t bytes = (size_t)c->n * sizeof(double);
-        PP_CUDA(cudaMemcpyAsync(c->wts, w, bytes, on_device ? cudaMemcpyDeviceToDevice
-                                                             : cudaMemcpyHostToDevice, c->stream));
+        PP_CUDA(cudaMemcpyAsync(c->wts, w, bytes, on_device == PP_MEM_DEVICE
+                                                      ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, c->stream));
         int bad = 0;
         PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
         PP_CUDA(launch_weights(c->wts, (int)c->n, c->w, c->wrel, c->err + 1, c->stream));
@@ -890,6 +983,14 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
     NvtxRange nvtx_("pp_set_state");
     if (pp_status s = check_ctx(c)) return s;
     if (!pos || !vel || !acc) return fail(PP_ERR_ARG, "pos, vel and acc are required");
+    if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
+    if (frame) {
+        if (!(std::isfinite(frame[0]) && std::isfinite(frame[1]) && std::isfinite(frame[2]) &&
+              std::isfinite(frame[3]) && frame[3] > 0))
+            return fail(PP_ERR_ARG, "invalid staging frame");
+        int e = 0;
+        if (std::frexp(frame[3], &e) != 0.5) return fail(PP_ERR_ARG, "frame scale must be a power of two");
+    }
     PP_CUDA(cudaSetDevice(c->device));
     drop_graphs(c);
     c->loaded = false;
@@ -898,30 +999,38 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
     if (st == PP_OK) st = import_aos(c, acc, on_device, c->a);
     if (st != PP_OK) return st;
     bool bad = false;
-    st = take_bad_input_flag(c, &bad);
-    if (st != PP_OK) return st;
-    if (bad) return fail(PP_ERR_ARG, "non-finite state");
     if (frame) {
-        if (!(std::isfinite(frame[0]) && std::isfinite(frame[1]) && std::isfinite(frame[2]) &&
-              std::isfinite(frame[3]) && frame[3] > 0))
-            return fail(PP_ERR_ARG, "invalid staging frame");
-        int e = 0;
-        if (std::frexp(frame[3], &e) != 0.5) return fail(PP_ERR_ARG, "frame scale must be a power of two");
+        // the frame is given: stage r_{n+1} = Eq. G(r_n, v_n, a_n) exactly as the
+        // step epilogue would, and check the input with the same synchronisation
         c->cx = frame[0];
         c->cy = frame[1];
         c->cz = frame[2];
         c->l0 = frame[3];
+        c->parity = 0;
+        st = restage_pending(c, false);
+        if (st == PP_OK) st = take_bad_input_flag(c, &bad);
+        if (st != PP_OK) return st;
+        if (bad) return fail(PP_ERR_ARG, "non-finite state");
     } else {
+        st = take_bad_input_flag(c, &bad);
+        if (st != PP_OK) return st;
+        if (bad) return fail(PP_ERR_ARG, "non-finite state");
         st = choose_frame(c);
         if (st != PP_OK) return st;
+        c->parity = 0;
+        st = restage_pending(c);
+        if (st != PP_OK) return st;
     }
-    // stage r_{n+1} = Eq. G(r_n, v_n, a_n) exactly as the step epilogue would
-    c->parity = 0;
-    st = restage_pending(c);
-    if (st != PP_OK) return st;
     c->loaded = true;
     c->step = step;
     return PP_OK;
+}
+
+pp_status pp_check_mapped(const void *p, int64_t bytes)
+{
+    if (bytes <= 0) return fail(PP_ERR_ARG, "bytes must be > 0");
+    const void *d = nullptr;
+    return mapped_view(p, (size_t)bytes, &d);
 }
 
 pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t *step,
@@ -929,6 +1038,7 @@ pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t
 {
     NvtxRange nvtx_("pp_get_state");
     if (pp_status s = check_ctx(c)) return s;
+    if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
     PP_CUDA(cudaSetDevice(c->device));
     pp_status st;
@@ -956,16 +1066,24 @@ pp_status pp_compute_fields(pp_ctx *c, double *E_out, int on_device)
     NvtxRange nvtx_("pp_compute_fields");
     if (pp_status s = check_ctx(c)) return s;
     if (!E_out) return fail(PP_ERR_ARG, "E_out is null");
+    if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
     PP_CUDA(cudaSetDevice(c->device));
+    double *target = E_out;
+    if (on_device == PP_MEM_HOST) {
+        target = c->aos;
+    } else if (on_device == PP_MEM_HOST_MAPPED) {
+        const void *d = nullptr;
+        if (pp_status st = mapped_view(E_out, (size_t)c->n * 3 * sizeof(double), &d)) return st;
+        target = static_cast<double *>(const_cast<void *>(d));
+    }
     // stage the current r_n into the idle buffer; the pending r_{n+1} stays put
     void *scratch = c->stage[c->parity ^ 1];
     pp_status st = stage_current(c, scratch, stage_kind(c));
     if (st != PP_OK) return st;
-    double *target = on_device ? E_out : c->aos;
     st = force_pass(c, MODE_FIELDS, scratch, nullptr, target);
     if (st != PP_OK) return st;
-    if (!on_device)
+    if (on_device == PP_MEM_HOST)
         PP_CUDA(cudaMemcpyAsync(E_out, c->aos, (size_t)c->n * 3 * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
     return check_device_errors(c, false);

@@ -147,25 +147,32 @@ cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaS
 
 namespace {
 
+// The [n][3] side is walked as a flat array of 3n doubles, so that a warp reads
+// (or writes) 32 consecutive doubles: this side may be host memory mapped into
+// the device address space, where every access crosses the CPU-GPU link.
 __global__ void aos_to_soa_kernel(const double *__restrict__ in, int n, double *x, double *y,
                                   double *z, int *bad)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double a = in[3 * (size_t)i], b = in[3 * (size_t)i + 1], c = in[3 * (size_t)i + 2];
-        if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(bad, 1);
-        x[i] = a;
-        y[i] = b;
-        z[i] = c;
+    const size_t total = 3 * (size_t)n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double a = in[t];
+        if (!isfinite(a)) atomicOr(bad, 1);
+        const size_t i = t / 3;
+        const int c = (int)(t - 3 * i);
+        (c == 0 ? x : c == 1 ? y : z)[i] = a;
     }
 }
 
 __global__ void soa_to_aos_kernel(const double *__restrict__ x, const double *__restrict__ y,
                                   const double *__restrict__ z, int n, double *out)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        out[3 * (size_t)i] = x[i];
-        out[3 * (size_t)i + 1] = y[i];
-        out[3 * (size_t)i + 2] = z[i];
+    const size_t total = 3 * (size_t)n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / 3;
+        const int c = (int)(t - 3 * i);
+        out[t] = (c == 0 ? x : c == 1 ? y : z)[i];
     }
 }
 
@@ -306,14 +313,14 @@ int grid_for(int n, int threads)
 cudaError_t launch_aos_to_soa(const double *in, int n, double *x, double *y, double *z, int *bad,
                               cudaStream_t s)
 {
-    aos_to_soa_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, x, y, z, bad);
+    aos_to_soa_kernel<<<grid_for(3 * n, 256), 256, 0, s>>>(in, n, x, y, z, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_soa_to_aos(const double *x, const double *y, const double *z, int n,
                               double *out, cudaStream_t s)
 {
-    soa_to_aos_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, z, n, out);
+    soa_to_aos_kernel<<<grid_for(3 * n, 256), 256, 0, s>>>(x, y, z, n, out);
     return cudaGetLastError();
 }
 

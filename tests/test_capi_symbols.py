@@ -45,3 +45,12 @@ def test_host_only_calls():
         assert "N must be" in str(e)
     else:
         raise AssertionError("N = 0 accepted")
+
+
+def test_binding_constants_match_the_header():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    values = dict(re.findall(r"\b(PP_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    assert {"PP_MEM_HOST", "PP_MEM_DEVICE", "PP_MEM_HOST_MAPPED", "PP_ACC_KAHAN",
+            "PP_POS_AUTO", "PP_ERR_STATE"} <= set(values)
+    for name, value in values.items():
+        assert getattr(capi, name) == int(value), name
