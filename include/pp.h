@@ -105,10 +105,36 @@ enum {
                                   the environment variable PP_TIMEOUT_NS at creation)        */
     PP_OPT_VARIANT = 6,        /* value: force-kernel variant index (-1 = automatic)          */
     PP_OPT_POSITIONS = 7,      /* value: a pp_positions (FP32 pair paths only)                 */
-    PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy, so
-                                  its bounded waits expire and the call returns
-                                  PP_ERR_TIMEOUT (tests the timeout path; no fault, no hang) */
+    PP_OPT_RESIDENT = 8,       /* value: a pp_resident (small-N stepping)                      */
+    PP_OPT_RESIDENT_ACTIVE = 9,/* pp_get_option only: 1 if pp_step now runs the resident kernel */
+    PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy (the
+                                  resident kernel: one grid-barrier arrival), so its bounded
+                                  waits expire and the call returns PP_ERR_TIMEOUT (tests the
+                                  timeout path; no fault, no hang) */
 };
+
+/* Resident small-N stepping (PP_OPT_RESIDENT).  The resident kernel runs all
+ * steps of a pp_step call in one cooperative launch: every CTA holds the
+ * whole staged source array in shared memory, computes the Eq. B sums of its
+ * targets (sources split over several threads per target, FP32 partials of at
+ * most 512 sources folded into FP64, the partials of a target added in a fixed
+ * order) and the Eq. G/H push, then meets the other CTAs at a grid-wide
+ * barrier (bounded wait: PP_ERR_TIMEOUT on expiry) before the next step.  It
+ * floors s = |d|^2 + eps^2 at 1e-24 in staged units (L0^2), so the self pair
+ * adds exactly 0 without a test per pair; for separations the FP32 staging
+ * resolves this changes s by less than one FP32 rounding.  Applicable with
+ * PP_ACC_FP64FOLD, PP_POS_SINGLE, equal weights and a packed-pair variant
+ * (the default, or a PP_OPT_VARIANT override with interleaved staging), for
+ * N <= 12288; PP_OPT_VARIANT otherwise still chooses the kernel of force
+ * passes and of per-launch steps (set PP_RESIDENT_OFF to step with it).
+ * Results differ from the per-launch kernels' at the FP32 rounding level
+ * (another summation order) and are bitwise reproducible on a given device. */
+typedef enum {
+    PP_RESIDENT_OFF = 0,   /* always the per-launch kernels */
+    PP_RESIDENT_AUTO = 1,  /* default: resident wherever applicable (measured faster than
+                              the per-launch kernels at every N up to 12288 on GB300) */
+    PP_RESIDENT_ON = 2     /* resident wherever applicable */
+} pp_resident;
 
 /*
  * Create a context for N macro-electrons of common weight w (Sec. 2.1 assumes

@@ -36,11 +36,17 @@ PP_OPT_GRAPH_BLOCK = 4
 PP_OPT_TIMEOUT_NS = 5
 PP_OPT_VARIANT = 6
 PP_OPT_POSITIONS = 7
+PP_OPT_RESIDENT = 8
+PP_OPT_RESIDENT_ACTIVE = 9
 
 PP_POS_SINGLE = 0
 PP_POS_SPLIT = 1
 PP_POS_AUTO = 2
 PP_OPT_TEST_SKIP_COPY = 99
+
+PP_RESIDENT_OFF = 0
+PP_RESIDENT_AUTO = 1
+PP_RESIDENT_ON = 2
 
 PP_MEM_HOST = 0
 PP_MEM_DEVICE = 1

@@ -55,6 +55,26 @@ const Variant *variants(int *count);
 // Launch one variant with the given arguments on `stream`.
 cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaStream_t stream);
 
+// Resident small-N stepping: all steps of one pp_step call in one cooperative
+// launch (pp_resident.cu).  The staged source array lives in each CTA's
+// shared memory.
+struct ResidentArgs {
+    void *stage[2];   // ping-pong staging (STAGE_F32I), npad entries each
+    int parity0;      // buffer holding the staged r_{n+1} at the first step
+    int nsteps;
+    int bt;           // targets per CTA (grid = ceil(n / bt))
+    int q;            // threads (source chunks) per target, bt * q <= threads per CTA
+    int chunk;        // sources per chunk, even
+    int nsrc;         // sources summed: n rounded up to even (the odd tail is padding)
+    unsigned *bar;    // grid-barrier arrival counter, zero at launch
+};
+// threads per CTA: 256 or 512 (the compiled instantiations)
+size_t resident_smem(int npad, int threads);
+cudaError_t resident_configure(int npad);
+cudaError_t resident_occupancy(int npad, int threads, int *blocks_per_sm);
+cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
+                            cudaStream_t stream);
+
 // Deterministic O(N) kernels.
 // AoS [n][3] -> three SoA arrays; sets *bad to 1 if any input is not finite.
 cudaError_t launch_aos_to_soa(const double *in, int n, double *x, double *y, double *z, int *bad,

@@ -1,0 +1,203 @@
+// pp_resident.cu -- small-N time stepping with every step of a pp_step call in
+// one cooperative launch: the Eq. B/E force sum and the Eq. G/H push of step
+// n+1 follow those of step n inside the same kernel, separated by a grid-wide
+// barrier, instead of one launch (and one j-split round trip through global
+// memory) per step.
+//
+// At small N a step of the per-launch kernels is bound by latency, not by the
+// FP32 pipe: CTA start-up, the first bulk copy, the partial-sum publication
+// and gather, and the launch itself cost more than the 11 FP32 lane
+// operations per pair.  Here each CTA keeps the whole staged source array in
+// shared memory (loaded once per step from L2), owns BT targets, and splits
+// the sources of each target over Q threads; the Q FP64 partials of a target
+// are added in a fixed order, and the push runs one (component, target) item
+// per thread.  The decomposition depends only on N and the SM count, so
+// results are bitwise reproducible on a given device.
+#include "pp_internal.h"
+
+namespace ppk {
+
+namespace {
+
+constexpr int kResFold = 512;   // sources per FP32 partial before the FP64 fold
+// Floor on s = |d|^2 + eps^2 (staged units): the self pair (d = 0 exactly)
+// then contributes rsqrt(s)^3 * 0 = 0 without a per-pair test, and for every
+// separation the FP32 staging resolves (|d| > 1e-8 L0) the floor changes s by
+// less than one FP32 rounding.  rsqrt(1e-24)^3 = 1e36 stays finite.
+constexpr float kSelfFloor = 1e-24f;
+
+// Grid-wide barrier of a cooperative launch.  Every CTA arrives once per
+// barrier; `target` is the arrival count that completes this one.  Thread 0
+// waits at most limit_ns; the verdict is shared with the CTA.
+__device__ bool grid_sync_bounded(unsigned *bar, unsigned target, uint64_t limit_ns, bool arrive,
+                                  int *s_flag)
+{
+    __syncthreads();   // the CTA's step writes happen before thread 0's release
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        const uint64_t t0 = globaltimer_ns();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                ok = 0;
+                break;
+            }
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();   // ... and before every thread's reads of the next step
+    return *s_flag != 0;
+}
+
+// One component of the MODE_STEP epilogue (finish_particle, component-wise):
+// a_{n+1} from the sum, Eq. G as staged, Eq. H, and the staged coordinate of
+// the next Eq. G.  Component 0 also writes the weight slot (equal weights: 1).
+__device__ __forceinline__ void finish_component(const ForceArgs &p, int i, int c, double sum,
+                                                 void *dst)
+{
+    double *const rc = c == 0 ? p.r[0] : c == 1 ? p.r[1] : p.r[2];
+    double *const vc = c == 0 ? p.v[0] : c == 1 ? p.v[1] : p.v[2];
+    double *const ac = c == 0 ? p.a[0] : c == 1 ? p.a[1] : p.a[2];
+    const double an = p.cscale * sum;
+    const double r0 = rc[i], v0 = vc[i], a0 = ac[i];
+    const double r1 = drift(r0, v0, a0, p.dt, p.half_dt2);   // Eq. G (as staged)
+    const double v1 = kick(v0, a0, an, p.half_dt);           // Eq. H
+    rc[i] = r1;
+    vc[i] = v1;
+    ac[i] = an;
+    const double rn = drift(r1, v1, an, p.dt, p.half_dt2);   // next Eq. G, staged only
+    const double cc = c == 0 ? p.cx : c == 1 ? p.cy : p.cz;
+    float *f = static_cast<float *>(dst) + 8 * (size_t)(i >> 1) + (i & 1);
+    f[2 * c] = __double2float_rn(staged_coord(rn, cc, p.inv_l0));
+    if (c == 0) f[6] = 1.0f;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+    force_resident_kernel(const ForceArgs p, const ResidentArgs ra)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *sj4 = reinterpret_cast<float4 *>(smem_raw);   // staged sources, interleaved pairs
+    const float *sj = reinterpret_cast<const float *>(smem_raw);
+    double *part = reinterpret_cast<double *>(smem_raw + (size_t)p.npad * sizeof(float4));
+    __shared__ int s_flag;
+
+    const int tid = threadIdx.x;
+    const int tl = tid % ra.bt, qi = tid / ra.bt;
+    const int i = blockIdx.x * ra.bt + tl;
+    const bool work = qi < ra.q && i < p.n;
+    const int j0 = min(qi * ra.chunk, ra.nsrc), j1 = min(j0 + ra.chunk, ra.nsrc);
+    const float eps2 = fmaxf(p.eps2f, kSelfFloor);
+    const f2_t EPS2 = f2_pack(eps2, eps2);
+
+    for (int s = 0; s < ra.nsteps; ++s) {
+        const int par = (ra.parity0 + s) & 1;
+        // other CTAs wrote these entries during the previous step: read through L2
+        const float4 *src = static_cast<const float4 *>(par ? ra.stage[1] : ra.stage[0]);
+        for (int k = tid; k < ra.nsrc; k += NT) sj4[k] = __ldcg(src + k);
+        __syncthreads();
+
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        if (work) {
+            const float *q = sj + 8 * (i >> 1) + (i & 1);
+            const f2_t X = f2_pack(q[0], q[0]), Y = f2_pack(q[2], q[2]), Z = f2_pack(q[4], q[4]);
+            for (int t0 = j0; t0 < j1; t0 += kResFold) {
+                const int t1 = min(t0 + kResFold, j1);
+                f2_t AX = 0ull, AY = 0ull, AZ = 0ull;
+#pragma unroll 4
+                for (int j = t0; j < t1; j += 2) {
+                    const float4 a = sj4[j];       // x_j x_j+1 y_j y_j+1
+                    const float4 b = sj4[j + 1];   // z_j z_j+1 w_j w_j+1
+                    const f2_t DX = f2_sub(X, f2_pack(a.x, a.y));
+                    const f2_t DY = f2_sub(Y, f2_pack(a.z, a.w));
+                    const f2_t DZ = f2_sub(Z, f2_pack(b.x, b.y));
+                    const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
+                    float s0, s1;
+                    f2_unpack(S, s0, s1);
+                    const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
+                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
+                    AX = f2_fma(INV3, DX, AX);
+                    AY = f2_fma(INV3, DY, AY);
+                    AZ = f2_fma(INV3, DZ, AZ);
+                }
+                float x0, x1, y0, y1, z0, z1;
+                f2_unpack(AX, x0, x1);
+                f2_unpack(AY, y0, y1);
+                f2_unpack(AZ, z0, z1);
+                sx += (double)(x0 + x1);
+                sy += (double)(y0 + y1);
+                sz += (double)(z0 + z1);
+            }
+        }
+        part[tid] = sx;
+        part[NT + tid] = sy;
+        part[2 * NT + tid] = sz;
+        __syncthreads();
+        // Epilogue, one (component, target) item per thread: the FP64 pipe runs
+        // at a small fraction of the FP32 rate here, so the sums and the push are
+        // spread over as many warps (and SM sub-partitions) as there are items.
+        for (int t = tid; t < 3 * ra.bt; t += NT) {
+            const int c = t / ra.bt, ti = t - c * ra.bt;
+            const int it = blockIdx.x * ra.bt + ti;
+            if (it >= p.n) continue;
+            double sum = 0.0;
+            for (int k = 0; k < ra.q; ++k) sum += part[c * NT + k * ra.bt + ti];   // fixed order
+            finish_component(p, it, c, sum, par ? ra.stage[0] : ra.stage[1]);
+        }
+        if (s + 1 < ra.nsteps || p.skip_copy) {
+            // test hook: CTA 0 withholds its first arrival, so every CTA's wait runs
+            // out (the barrier is then taken after a last step too)
+            const bool arrive = !(p.skip_copy && blockIdx.x == 0 && s == 0);
+            if (!grid_sync_bounded(ra.bar, gridDim.x * (unsigned)(s + 1), p.timeout_ns, arrive,
+                                   &s_flag)) {
+                if (tid == 0) atomicOr(p.err, 1);
+                return;
+            }
+        }
+    }
+}
+
+const void *resident_fn(int threads)
+{
+    return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512>)
+                          : reinterpret_cast<const void *>(&force_resident_kernel<256>);
+}
+
+}  // namespace
+
+size_t resident_smem(int npad, int threads)
+{
+    return (size_t)npad * sizeof(float4) + 3 * (size_t)threads * sizeof(double);
+}
+
+cudaError_t resident_configure(int npad)
+{
+    for (int threads : {256, 512}) {
+        cudaError_t e = cudaFuncSetAttribute(resident_fn(threads),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)resident_smem(npad, threads));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t resident_occupancy(int npad, int threads, int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, resident_fn(threads),
+                                                         threads, resident_smem(npad, threads));
+}
+
+cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
+                            cudaStream_t stream)
+{
+    ForceArgs ca = a;
+    ResidentArgs cr = ra;
+    void *args[] = {&ca, &cr};
+    return cudaLaunchCooperativeKernel(resident_fn(threads), dim3(grid), dim3(threads), args,
+                                       resident_smem(a.npad, threads), stream);
+}
+
+}  // namespace ppk

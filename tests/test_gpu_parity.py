@@ -211,13 +211,16 @@ def test_coincident_particles_without_softening():
                  report="coincident")
 
 
-def test_run_matches_oracle_cold_gaussian_2048():
-    """The 2048-electron cold Gaussian, no softening, dt = 1e-16 s, all 200 steps."""
+@pytest.mark.parametrize("resident", [capi.PP_RESIDENT_AUTO, capi.PP_RESIDENT_OFF])
+def test_run_matches_oracle_cold_gaussian_2048(resident):
+    """The 2048-electron cold Gaussian, no softening, dt = 1e-16 s, all 200 steps: with
+    the resident small-N kernel (the default at this N) and with per-launch kernels."""
     b = wl.COLD_GAUSSIAN_2048
     pos0 = b.positions()
     vel0 = b.velocities()
     p_ref, v_ref, a_ref = oracle.vv_run(pos0, vel0, None, b.w, b.eps, b.dt, b.steps)
     with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+        sim.set_option(capi.PP_OPT_RESIDENT, resident)
         sim.load(pos0, vel0)
         sim.step(b.steps)
         p, v, a, step, _ = sim.state()
@@ -273,6 +276,7 @@ def test_step_with_and_without_graphs_is_bitwise_equal():
     out = []
     for gb in (0, 8):
         with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+            sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)   # per-launch steps
             sim.set_option(capi.PP_OPT_GRAPH_BLOCK, gb)
             sim.load(pos0)
             sim.step(37)
@@ -299,16 +303,19 @@ def test_diagnostics_match_oracle():
     assert abs(d["pe"] / pe - 1) <= FORCE_TOL
 
 
-def test_checkpoint_resume_is_bitwise():
+@pytest.mark.parametrize("resident", [capi.PP_RESIDENT_AUTO, capi.PP_RESIDENT_OFF])
+def test_checkpoint_resume_is_bitwise(resident):
     n, w, eps, dt = 3000, 50.0, 1e-9, 2e-15
     pos0 = wl.uniform_sphere(n, 5e-6, seed=38)
     with capi.Simulation(n, w, dt, eps) as a:
+        a.set_option(capi.PP_OPT_RESIDENT, resident)
         a.load(pos0)
         a.step(10)
         p, v, acc, step, frame = a.state()
         a.step(15)
         ref = a.state()
     with capi.Simulation(n, w, dt, eps) as b:
+        b.set_option(capi.PP_OPT_RESIDENT, resident)
         b.set_state(p, v, acc, step, frame)
         b.step(15)
         got = b.state()
@@ -402,12 +409,14 @@ def test_invalid_arguments_and_states():
 def test_bounded_wait_reports_timeout_and_context_recovers(variant):
     """A withheld tile copy makes the kernel's bounded waits run out: the call returns
     PP_ERR_TIMEOUT (no fault, no hang) and the context works again after a reload.
-    Covered for the default plan, a scalar kernel, the shared-memory-fold packed kernel
-    and the thread-block-cluster kernel (whose CTAs still meet at both cluster barriers)."""
+    Covered for the default plan (the resident kernel at this N: a withheld grid-barrier
+    arrival), a scalar kernel, the shared-memory-fold packed kernel and the
+    thread-block-cluster kernel (whose CTAs still meet at both cluster barriers)."""
     n = 3000
     pos = wl.gaussian_bunch(n, 2e-6, seed=41)
     with capi.Simulation(n, 1.0, 1e-15, 1e-9) as sim:
-        if variant is not None:
+        if variant is not None:   # step with this kernel, not the resident small-N one
+            sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
             sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index(variant))
         sim.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
         sim.load(pos)
