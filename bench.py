@@ -60,6 +60,8 @@ def parse():
                     help="requests of the bounded serving trace (0 = skip)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 2^20-particle and all-FP64 comparison measurements")
+    ap.add_argument("--lattice-steps", type=int, default=2000,
+                    help="steps of the paper's 16^3 lattice, resident and per-launch (0 = skip)")
     return ap.parse_args()
 
 
@@ -235,6 +237,32 @@ def run_extras(sms: int, peak_tflops: float):
         out["fp64_path"] = {"workload": g.name, "pairs_per_s": float(g.n) ** 2 / sec,
                             "ms_per_step": sec * 1e3,
                             "note": "FP64 pair math and accumulation, one step"}
+    return out
+
+
+def run_paper_lattice(steps: int):
+    """The paper's own workload (Sec. 2.1): the 16^3 cube lattice, eps = 0, dt = 1e-13 s,
+    stepped with the library's default small-N path (the resident kernel: all steps of
+    one call in one cooperative launch), against per-launch kernels with CUDA graphs."""
+    import torch
+    from paper_2502_10640_gb300 import capi
+    b = wl.PAPER_LATTICE
+    out = {"workload": b.name, "steps": steps, "paper_run_steps": b.steps}
+    for label, mode in (("resident", capi.PP_RESIDENT_AUTO), ("per_launch", capi.PP_RESIDENT_OFF)):
+        with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:
+            sim.set_option(capi.PP_OPT_RESIDENT, mode)
+            sim.load(b.positions())
+            sim.step(16)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step(steps)
+            sec = (time.perf_counter() - t0) / steps
+            out[f"{label}_us_per_step"] = sec * 1e6
+            if label == "resident":
+                out["resident_active"] = bool(sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE))
+                out["paper_run_s"] = sec * b.steps
+                out["pairs_per_s"] = float(b.n) ** 2 / sec
+    out["timing"] = "host wall clock around one synchronous pp_step call"
     return out
 
 
@@ -433,6 +461,7 @@ def run_ours(args):
         pk, _ = load_peaks()
         extras = run_extras(sms, fp32_peak_tflops(sms, float(pk.get("sm_max_mhz", 2070.0))))
     served = run_serving(args.serve_requests) if (args.serve_requests > 0 and world == 1) else None
+    lattice = run_paper_lattice(args.lattice_steps) if (args.lattice_steps > 0 and world == 1) else None
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -471,6 +500,8 @@ def run_ours(args):
         line["batched"] = batched
     if served:
         line["serving"] = served
+    if lattice:
+        line["paper_lattice"] = lattice
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
