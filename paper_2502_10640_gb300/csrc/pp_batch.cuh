@@ -14,10 +14,13 @@
 
 namespace ppk {
 
-constexpr int kBatchT = 128, kBatchR = 4, kBatchTile = 512, kBatchStages = 3, kBatchMinB = 4;
-constexpr int kBatchUnroll = 2;   // pair-loop unroll of tile_packed: 2 measured 15% faster than 1 here
+// 1024-source tiles in a two-stage ring and the pair loop unrolled twice:
+// measured fastest for this kernel on the 64-bunch mix (unrolling once, which
+// suits the single-bunch kernel, is 13 % slower here).
+constexpr int kBatchT = 128, kBatchR = 4, kBatchTile = 1024, kBatchStages = 2, kBatchMinB = 4;
+constexpr int kBatchUnroll = 2;
 constexpr int kBatchBI = kBatchT * kBatchR;
-constexpr int kBatchJChunk = 16 * kBatchTile;   // sources per work item
+constexpr int kBatchJChunk = 8192;   // sources per work item (a multiple of the tile)
 
 // One bunch as the batch kernel sees it (device memory, rewritten by the host
 // between step blocks).
@@ -38,6 +41,42 @@ struct BatchHeader {
     int nbunch;
     int nitems;
 };
+
+// Full kernel arguments of one bunch for the current step.
+__device__ __forceinline__ ForceArgs item_args(const BunchDesc &d, int par, int *err,
+                                               unsigned long long timeout_ns, int skip)
+{
+    ForceArgs p{};
+    p.src = d.stage[par];
+    p.dst = d.stage[par ^ 1];
+    p.n = d.n;
+    p.npad = d.npad;
+    p.nib = d.nib;
+    p.nsplit = d.nsplit;
+    p.jchunk = d.jchunk;
+    p.mode = d.mode;
+    p.eps2f = d.eps2f;
+    p.partial = d.partial;
+    p.tickets = d.tickets;
+    p.nipad = d.nipad;
+    for (int c = 0; c < 3; ++c) {
+        p.r[c] = d.r[c];
+        p.v[c] = d.v[c];
+        p.a[c] = d.a[c];
+    }
+    p.cscale = d.cscale;
+    p.dt = d.dt;
+    p.half_dt = d.half_dt;
+    p.half_dt2 = d.half_dt2;
+    p.cx = d.cx;
+    p.cy = d.cy;
+    p.cz = d.cz;
+    p.inv_l0 = d.inv_l0;
+    p.err = err;
+    p.timeout_ns = timeout_ns;
+    p.skip_copy = skip;
+    return p;
+}
 
 template <int T, int R, int TILE, int STAGES, int MINB>
 __global__ void __launch_bounds__(T, MINB)
@@ -82,35 +121,18 @@ __global__ void __launch_bounds__(T, MINB)
         const int split = local / d.nib;
         const int par = (d.parity0 + step_k) & 1;
 
+        // Arguments of the tile loop only: the epilogue's arguments are read from
+        // the descriptor again after the loop, so they hold no registers during it.
+        const int skip = (skip_copy && item == 0) ? 2 : 0;   // test hook: item 0 loses a tile
         ForceArgs p{};
         p.src = d.stage[par];
-        p.dst = d.stage[par ^ 1];
         p.n = d.n;
         p.npad = d.npad;
-        p.nib = d.nib;
-        p.nsplit = d.nsplit;
         p.jchunk = d.jchunk;
-        p.mode = d.mode;
         p.eps2f = d.eps2f;
-        p.partial = d.partial;
-        p.tickets = d.tickets;
-        p.nipad = d.nipad;
-        for (int c = 0; c < 3; ++c) {
-            p.r[c] = d.r[c];
-            p.v[c] = d.v[c];
-            p.a[c] = d.a[c];
-        }
-        p.cscale = d.cscale;
-        p.dt = d.dt;
-        p.half_dt = d.half_dt;
-        p.half_dt2 = d.half_dt2;
-        p.cx = d.cx;
-        p.cy = d.cy;
-        p.cz = d.cz;
-        p.inv_l0 = d.inv_l0;
         p.err = err;
         p.timeout_ns = timeout_ns;
-        p.skip_copy = (skip_copy && item == 0) ? 2 : 0;   // test hook: item 0 loses a tile
+        p.skip_copy = skip;
 
         const int i0 = ib * BI;
         const int j0 = split * p.jchunk;
@@ -164,6 +186,7 @@ __global__ void __launch_bounds__(T, MINB)
             return;
         }
         g += ntiles;
+        const ForceArgs pe = item_args(descs[lo], par, err, timeout_ns, skip);
         double ax64[R], ay64[R], az64[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -172,14 +195,14 @@ __global__ void __launch_bounds__(T, MINB)
             az64[r] = sacc[2 * BI + r * T + tid];
         }
         bool finish = true;
-        if (p.nsplit > 1) {
-            finish = split_publish<T, R>(p, ib, split, ax64, ay64, az64, 3, &s_flag);
-            if (finish) split_gather<T, R>(p, ib, ax64, ay64, az64, 3);
+        if (pe.nsplit > 1) {
+            finish = split_publish<T, R>(pe, ib, split, ax64, ay64, az64, 3, &s_flag);
+            if (finish) split_gather<T, R>(pe, ib, ax64, ay64, az64, 3);
         }
         if (finish) {
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                finish_particle<STAGE_F32I>(p, i0 + r * T + tid, ax64[r], ay64[r], az64[r]);
+                finish_particle<STAGE_F32I>(pe, i0 + r * T + tid, ax64[r], ay64[r], az64[r]);
         }
         __syncthreads();  // s_item and the shared accumulators are reused next
     }
