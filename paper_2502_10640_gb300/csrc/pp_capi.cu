@@ -1100,11 +1100,39 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
     PP_CUDA(cudaSetDevice(c->device));
     drop_graphs(c);
     c->loaded = false;
+    bool bad = false;
+    if (frame && on_device != PP_MEM_HOST) {
+        // device or mapped host buffers: one pass converts the state, checks it and
+        // stages r_{n+1} = Eq. G(r_n, v_n, a_n); one synchronisation
+        const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+        const double *src[3] = {pos, vel, acc};
+        if (on_device == PP_MEM_HOST_MAPPED) {
+            for (auto &q : src) {
+                const void *d = nullptr;
+                if (pp_status st = mapped_view(q, bytes, &d)) return st;
+                q = static_cast<const double *>(d);
+            }
+        }
+        c->cx = frame[0];
+        c->cy = frame[1];
+        c->cz = frame[2];
+        c->l0 = frame[3];
+        c->parity = 0;
+        PP_CUDA(launch_fill_padding(c->stage[1], (int)c->n, c->npad, stage_kind(c), c->stream));
+        PP_CUDA(launch_import_state(src[0], src[1], src[2], (int)c->n, c->npad, c->r, c->v, c->a,
+                                    c->stage[0], stage_kind(c), c->dt, c->dt * c->dt / 2.0, c->cx,
+                                    c->cy, c->cz, 1.0 / c->l0, c->wrel, c->err + 1, c->stream));
+        pp_status st = take_bad_input_flag(c, &bad);
+        if (st != PP_OK) return st;
+        if (bad) return fail(PP_ERR_ARG, "non-finite state");
+        c->loaded = true;
+        c->step = step;
+        return PP_OK;
+    }
     pp_status st = import_aos(c, pos, on_device, c->r);
     if (st == PP_OK) st = import_aos(c, vel, on_device, c->v);
     if (st == PP_OK) st = import_aos(c, acc, on_device, c->a);
     if (st != PP_OK) return st;
-    bool bad = false;
     if (frame) {
         // the frame is given: stage r_{n+1} = Eq. G(r_n, v_n, a_n) exactly as the
         // step epilogue would, and check the input with the same synchronisation
@@ -1148,9 +1176,26 @@ pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t
     if (!c->loaded) return fail(PP_ERR_STATE, "no particles loaded");
     PP_CUDA(cudaSetDevice(c->device));
     pp_status st;
-    if (pos && (st = export_aos(c, c->r, pos, on_device)) != PP_OK) return st;
-    if (vel && (st = export_aos(c, c->v, vel, on_device)) != PP_OK) return st;
-    if (acc && (st = export_aos(c, c->a, acc, on_device)) != PP_OK) return st;
+    if (on_device != PP_MEM_HOST) {
+        // device or mapped host buffers: one pass writes all requested arrays
+        const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+        double *dst[3] = {pos, vel, acc};
+        if (on_device == PP_MEM_HOST_MAPPED) {
+            for (auto &q : dst) {
+                if (!q) continue;
+                const void *d = nullptr;
+                if ((st = mapped_view(q, bytes, &d)) != PP_OK) return st;
+                q = static_cast<double *>(const_cast<void *>(d));
+            }
+        }
+        if (dst[0] || dst[1] || dst[2])
+            PP_CUDA(launch_export_state(c->r, c->v, c->a, (int)c->n, dst[0], dst[1], dst[2],
+                                        c->stream));
+    } else {
+        if (pos && (st = export_aos(c, c->r, pos, on_device)) != PP_OK) return st;
+        if (vel && (st = export_aos(c, c->v, vel, on_device)) != PP_OK) return st;
+        if (acc && (st = export_aos(c, c->a, acc, on_device)) != PP_OK) return st;
+    }
     if (step) *step = c->step;
     if (frame) {
         frame[0] = c->cx;

@@ -102,6 +102,18 @@ cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *c
                                double cx, double cy, double cz, double inv_l0, cudaStream_t s,
                                const float *wrel = nullptr);
 
+// Whole-state import (pp_set_state): [n][3] r, v, a (device-accessible) ->
+// SoA state + *bad flag + drift(r, v, a) staged into dst with its padding.
+cudaError_t launch_import_state(const double *pos, const double *vel, const double *acc, int n,
+                                int npad, double *const r[3], double *const v[3],
+                                double *const a[3], void *dst, int kind, double dt,
+                                double half_dt2, double cx, double cy, double cz, double inv_l0,
+                                const float *wrel, int *bad, cudaStream_t s);
+// Whole-state export (pp_get_state): SoA r, v, a -> [n][3] device-accessible
+// arrays; null outputs are skipped.
+cudaError_t launch_export_state(double *const r[3], double *const v[3], double *const a[3], int n,
+                                double *pos, double *vel, double *acc, cudaStream_t s);
+
 // Moments over n particles in a fixed reduction order.
 //  pass 0: sums of x, y, z                                     -> out[0..2]
 //  pass 1: sum |r-c|^2, sum w|v|^2, sum w vx, w vy, w vz, sum x^2,

@@ -176,6 +176,65 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ x, const double *__
     }
 }
 
+// Whole-state import for pp_set_state: r, v, a as [n][3] (device memory or
+// mapped host memory) -> SoA state, finiteness flag, and the pending Eq. G
+// positions drift(r, v, a) staged into dst (padding entries n..npad-1
+// included), in one pass.  One thread per particle.
+template <int KIND>
+__global__ void import_state_kernel(const double *__restrict__ pos, const double *__restrict__ vel,
+                                    const double *__restrict__ acc, int n, int npad, double *rx,
+                                    double *ry, double *rz, double *vx, double *vy, double *vz,
+                                    double *ax, double *ay, double *az, void *dst, double dt,
+                                    double half_dt2, double cx, double cy, double cz,
+                                    double inv_l0, const float *__restrict__ wrel, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+        if (i >= n) {
+            store_padding<KIND>(dst, npad, i);
+            continue;
+        }
+        const size_t b = 3 * (size_t)i;
+        const double r0 = pos[b], r1 = pos[b + 1], r2 = pos[b + 2];
+        const double v0 = vel[b], v1 = vel[b + 1], v2 = vel[b + 2];
+        const double a0 = acc[b], a1 = acc[b + 1], a2 = acc[b + 2];
+        if (!(isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(v0) && isfinite(v1) &&
+              isfinite(v2) && isfinite(a0) && isfinite(a1) && isfinite(a2)))
+            atomicOr(bad, 1);
+        rx[i] = r0; ry[i] = r1; rz[i] = r2;
+        vx[i] = v0; vy[i] = v1; vz[i] = v2;
+        ax[i] = a0; ay[i] = a1; az[i] = a2;
+        store_staged<KIND>(dst, npad, i, drift(r0, v0, a0, dt, half_dt2),
+                           drift(r1, v1, a1, dt, half_dt2), drift(r2, v2, a2, dt, half_dt2), cx,
+                           cy, cz, inv_l0, wrel ? wrel[i] : 1.0f);
+    }
+}
+
+// Whole-state export for pp_get_state: up to three SoA triples -> [n][3]
+// arrays (device memory or mapped host memory; a null output is skipped), in
+// one pass walked as flat arrays so that a warp writes 32 consecutive doubles.
+__global__ void export_state_kernel(const double *__restrict__ rx, const double *__restrict__ ry,
+                                    const double *__restrict__ rz, const double *__restrict__ vx,
+                                    const double *__restrict__ vy, const double *__restrict__ vz,
+                                    const double *__restrict__ ax, const double *__restrict__ ay,
+                                    const double *__restrict__ az, int n, double *pos,
+                                    double *vel, double *acc)
+{
+    const size_t per = 3 * (size_t)n, total = 3 * per;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int arr = (int)(t / per);
+        const size_t f = t - arr * per;
+        double *out = arr == 0 ? pos : arr == 1 ? vel : acc;
+        if (!out) continue;
+        const size_t i = f / 3;
+        const int c = (int)(f - 3 * i);
+        const double *src = arr == 0 ? (c == 0 ? rx : c == 1 ? ry : rz)
+                          : arr == 1 ? (c == 0 ? vx : c == 1 ? vy : vz)
+                                     : (c == 0 ? ax : c == 1 ? ay : az);
+        out[f] = src[i];
+    }
+}
+
 template <int KIND>
 __global__ void stage_kernel(const double *__restrict__ x, const double *__restrict__ y,
                              const double *__restrict__ z, int n, int npad, void *dst, double cx,
@@ -375,6 +434,32 @@ cudaError_t launch_stage_drift(double *const r[3], double *const v[3], double *c
     else if (kind == STAGE_F32X2) stage_drift_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_SD_ARGS);
     else stage_drift_kernel<STAGE_F64><<<g, 256, 0, s>>>(PP_SD_ARGS);
 #undef PP_SD_ARGS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_state(const double *pos, const double *vel, const double *acc, int n,
+                                int npad, double *const r[3], double *const v[3],
+                                double *const a[3], void *dst, int kind, double dt,
+                                double half_dt2, double cx, double cy, double cz, double inv_l0,
+                                const float *wrel, int *bad, cudaStream_t s)
+{
+    const int g = grid_for(npad, 256);
+#define PP_IS_ARGS pos, vel, acc, n, npad, r[0], r[1], r[2], v[0], v[1], v[2], a[0], a[1], a[2], \
+                   dst, dt, half_dt2, cx, cy, cz, inv_l0, wrel, bad
+    if (kind == STAGE_F32IX2) import_state_kernel<STAGE_F32IX2><<<g, 256, 0, s>>>(PP_IS_ARGS);
+    else if (kind == STAGE_F32I) import_state_kernel<STAGE_F32I><<<g, 256, 0, s>>>(PP_IS_ARGS);
+    else if (kind == STAGE_F32) import_state_kernel<STAGE_F32><<<g, 256, 0, s>>>(PP_IS_ARGS);
+    else if (kind == STAGE_F32X2) import_state_kernel<STAGE_F32X2><<<g, 256, 0, s>>>(PP_IS_ARGS);
+    else import_state_kernel<STAGE_F64><<<g, 256, 0, s>>>(PP_IS_ARGS);
+#undef PP_IS_ARGS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_state(double *const r[3], double *const v[3], double *const a[3], int n,
+                                double *pos, double *vel, double *acc, cudaStream_t s)
+{
+    export_state_kernel<<<grid_for(3 * n, 256), 256, 0, s>>>(r[0], r[1], r[2], v[0], v[1], v[2],
+                                                            a[0], a[1], a[2], n, pos, vel, acc);
     return cudaGetLastError();
 }
 

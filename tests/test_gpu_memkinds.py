@@ -119,3 +119,23 @@ def test_batch_accepts_every_kind_and_refuses_others():
         c = b.state(slot.value, N)
         for x, y in zip(a[:3], c[:3]):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kind", ["device", "mapped"])
+def test_set_state_refuses_non_finite_device_side_input(kind):
+    """The one-pass state import checks finiteness on the device: a NaN velocity in a
+    device or mapped buffer is refused with PP_ERR_ARG and a reload recovers."""
+    pos, vel = _bunch()
+    conv = {"device": _device, "mapped": _pinned}[kind]
+    with capi.Simulation(N, 7.0, 2e-15, 1e-9) as sim:
+        sim.load(pos, vel)
+        p, v, a, step, frame = sim.state()
+        v[123, 1] = np.nan
+        with pytest.raises(capi.PPError) as e:
+            sim.set_state(conv(p), conv(v), conv(a), step, frame)
+        assert e.value.status == capi.PP_ERR_ARG
+        with pytest.raises(capi.PPError) as e:
+            sim.step(1)
+        assert e.value.status == capi.PP_ERR_STATE
+        sim.load(pos, vel)
+        sim.step(2)
