@@ -734,7 +734,7 @@ ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
     // one CTA per SM at most, and at least 8 targets per CTA
     const int64_t g0 = std::min<int64_t>((int64_t)c->sms, std::max<int64_t>(1, (c->n + 7) / 8));
     rp.bt = (int)((c->n + g0 - 1) / g0);
-    if (rp.bt > threads) return rp;
+    if (3 * rp.bt > threads) return rp;   // one thread per (component, target) item
     rp.grid = (int)((c->n + rp.bt - 1) / rp.bt);
     if (rp.grid > c->sms * occ) return rp;
     rp.nsrc = (int)round_up(c->n, 2);

@@ -11,7 +11,8 @@
 // shared memory (loaded once per step from L2), owns BT targets, and splits
 // the sources of each target over Q threads; the Q FP64 partials of a target
 // are added in a fixed order, and the push runs one (component, target) item
-// per thread.  The decomposition depends only on N and the SM count, so
+// per thread, which keeps that item's FP64 r, v, a in registers for the whole
+// launch.  The decomposition depends only on N and the SM count, so
 // results are bitwise reproducible on a given device.
 #include "pp_internal.h"
 
@@ -52,24 +53,21 @@ __device__ bool grid_sync_bounded(unsigned *bar, unsigned target, uint64_t limit
     return *s_flag != 0;
 }
 
-// One component of the MODE_STEP epilogue (finish_particle, component-wise):
-// a_{n+1} from the sum, Eq. G as staged, Eq. H, and the staged coordinate of
-// the next Eq. G.  Component 0 also writes the weight slot (equal weights: 1).
-__device__ __forceinline__ void finish_component(const ForceArgs &p, int i, int c, double sum,
-                                                 void *dst)
+// One component of the MODE_STEP epilogue (finish_particle, component-wise),
+// on state held in registers: a_{n+1} from the sum, Eq. G as staged, Eq. H,
+// and the staged coordinate of the next Eq. G.  Component 0 also writes the
+// weight slot (equal weights: 1).
+__device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c, double cc,
+                                               double sum, double &r, double &v, double &a,
+                                               void *dst)
 {
-    double *const rc = c == 0 ? p.r[0] : c == 1 ? p.r[1] : p.r[2];
-    double *const vc = c == 0 ? p.v[0] : c == 1 ? p.v[1] : p.v[2];
-    double *const ac = c == 0 ? p.a[0] : c == 1 ? p.a[1] : p.a[2];
     const double an = p.cscale * sum;
-    const double r0 = rc[i], v0 = vc[i], a0 = ac[i];
-    const double r1 = drift(r0, v0, a0, p.dt, p.half_dt2);   // Eq. G (as staged)
-    const double v1 = kick(v0, a0, an, p.half_dt);           // Eq. H
-    rc[i] = r1;
-    vc[i] = v1;
-    ac[i] = an;
+    const double r1 = drift(r, v, a, p.dt, p.half_dt2);   // Eq. G (as staged)
+    const double v1 = kick(v, a, an, p.half_dt);          // Eq. H
+    r = r1;
+    v = v1;
+    a = an;
     const double rn = drift(r1, v1, an, p.dt, p.half_dt2);   // next Eq. G, staged only
-    const double cc = c == 0 ? p.cx : c == 1 ? p.cy : p.cz;
     float *f = static_cast<float *>(dst) + 8 * (size_t)(i >> 1) + (i & 1);
     f[2 * c] = __double2float_rn(staged_coord(rn, cc, p.inv_l0));
     if (c == 0) f[6] = 1.0f;
@@ -92,6 +90,24 @@ __global__ void __launch_bounds__(NT, 1)
     const int j0 = min(qi * ra.chunk, ra.nsrc), j1 = min(j0 + ra.chunk, ra.nsrc);
     const float eps2 = fmaxf(p.eps2f, kSelfFloor);
     const f2_t EPS2 = f2_pack(eps2, eps2);
+
+    // Each (component, target) item of the CTA belongs to one thread for the
+    // whole launch (3 BT <= threads): that thread alone reads and writes the
+    // item's r, v, a, so it keeps them in registers and stores them once at
+    // the end.
+    const int oc = tid / ra.bt, oti = tid - oc * ra.bt;
+    const int oi = blockIdx.x * ra.bt + oti;
+    const bool owner = tid < 3 * ra.bt && oi < p.n;
+    double *const rc = oc == 0 ? p.r[0] : oc == 1 ? p.r[1] : p.r[2];
+    double *const vc = oc == 0 ? p.v[0] : oc == 1 ? p.v[1] : p.v[2];
+    double *const ac = oc == 0 ? p.a[0] : oc == 1 ? p.a[1] : p.a[2];
+    const double occ = oc == 0 ? p.cx : oc == 1 ? p.cy : p.cz;
+    double r_o = 0.0, v_o = 0.0, a_o = 0.0;
+    if (owner) {
+        r_o = rc[oi];
+        v_o = vc[oi];
+        a_o = ac[oi];
+    }
 
     for (int s = 0; s < ra.nsteps; ++s) {
         const int par = (ra.parity0 + s) & 1;
@@ -139,13 +155,10 @@ __global__ void __launch_bounds__(NT, 1)
         // Epilogue, one (component, target) item per thread: the FP64 pipe runs
         // at a small fraction of the FP32 rate here, so the sums and the push are
         // spread over as many warps (and SM sub-partitions) as there are items.
-        for (int t = tid; t < 3 * ra.bt; t += NT) {
-            const int c = t / ra.bt, ti = t - c * ra.bt;
-            const int it = blockIdx.x * ra.bt + ti;
-            if (it >= p.n) continue;
+        if (owner) {
             double sum = 0.0;
-            for (int k = 0; k < ra.q; ++k) sum += part[c * NT + k * ra.bt + ti];   // fixed order
-            finish_component(p, it, c, sum, par ? ra.stage[0] : ra.stage[1]);
+            for (int k = 0; k < ra.q; ++k) sum += part[oc * NT + k * ra.bt + oti];   // fixed order
+            push_component(p, oi, oc, occ, sum, r_o, v_o, a_o, par ? ra.stage[0] : ra.stage[1]);
         }
         if (s + 1 < ra.nsteps || p.skip_copy) {
             // test hook: CTA 0 withholds its first arrival, so every CTA's wait runs
@@ -154,9 +167,14 @@ __global__ void __launch_bounds__(NT, 1)
             if (!grid_sync_bounded(ra.bar, gridDim.x * (unsigned)(s + 1), p.timeout_ns, arrive,
                                    &s_flag)) {
                 if (tid == 0) atomicOr(p.err, 1);
-                return;
+                return;   // the state is left unspecified (the call reports the timeout)
             }
         }
+    }
+    if (owner) {
+        rc[oi] = r_o;
+        vc[oi] = v_o;
+        ac[oi] = a_o;
     }
 }
 
