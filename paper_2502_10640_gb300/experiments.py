@@ -4,7 +4,8 @@ The electron bunch is the cell-centred cube lattice of Sec. 2.1 (edge 0.1 mm, de
 5e16 m^-3, at rest), run to 1e-8 s:
   * time-step sweep (Fig. 2a): N_p = 16^3, dt in {1e-13, 1e-12, 1e-11, 1e-10} s;
   * particle-number sweep (Fig. 2b): N_p in {4^3, 8^3, 16^3, 32^3}, dt = 1e-13 s;
-recording the emittance of Eq. I and the moments of Figs. 5-6 along the way.  The runs
+recording the emittance of Eq. I and the moments of Figs. 5-6 along the way, and the
+relative change of the total energy (kinetic + Coulomb potential) over each run.  The runs
 use the hot path unchanged (pp_step) and only add diagnostics over time.
 
     python -m paper_2502_10640_gb300.experiments [--t-end 1e-8] [--records 200] [--out DIR]
@@ -41,15 +42,20 @@ def run_lattice(n_side: int, dt: float, t_end: float, records: int = 200,
         sim.load(pos)
         t0 = time.perf_counter()
         done = 0
-        series.append(sim.diagnostics(with_pe=False))
+        first = sim.diagnostics(with_pe=True)
+        series.append(first)
         while done < steps:
             k = min(every, steps - done)
             sim.step(k)
             done += k
-            series.append(sim.diagnostics(with_pe=False))
+            series.append(sim.diagnostics(with_pe=done == steps))
         wall = time.perf_counter() - t0
+        resident = bool(sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE))
+    last = series[-1]
+    e0, e1 = first["ke"] + first["pe"], last["ke"] + last["pe"]
     return {"n_side": n_side, "n": n, "w": w, "dt": dt, "steps": steps, "wall_s": wall,
-            "pairs_per_s": float(n) * n * steps / wall,
+            "pairs_per_s": float(n) * n * steps / wall, "resident": resident,
+            "energy_drift": (e1 - e0) / abs(e0),
             "series": {k: [d[k] for d in series] for k in FIELDS}}
 
 
@@ -79,8 +85,12 @@ def main(argv=None):
         run = run_lattice(k, dt, args.t_end, args.records)
         name = f"lattice{k}_dt{dt:.0e}.csv"
         write_csv(os.path.join(args.out, name), run)
-        row = {kk: run[kk] for kk in ("n_side", "n", "w", "dt", "steps", "wall_s", "pairs_per_s")}
-        row.update(sweep=sweep, file=name, final_emit_x=run["series"]["emit_x"][-1])
+        row = {kk: run[kk] for kk in ("n_side", "n", "w", "dt", "steps", "wall_s", "pairs_per_s",
+                                      "resident", "energy_drift")}
+        ser = run["series"]
+        row.update(sweep=sweep, file=name, final_emit_x=ser["emit_x"][-1],
+                   x_rms_growth=ser["x_rms"][-1] / ser["x_rms"][0],
+                   final_vx_max=ser["vx_max"][-1])
         summary.append(row)
         print(json.dumps(row), flush=True)
     with open(os.path.join(args.out, "summary.json"), "w") as f:
