@@ -123,7 +123,8 @@ enum {
  * floors s = |d|^2 + eps^2 at 1e-24 in staged units (L0^2), so the self pair
  * adds exactly 0 without a test per pair; for separations the FP32 staging
  * resolves this changes s by less than one FP32 rounding.  Applicable with
- * PP_ACC_FP64FOLD, PP_POS_SINGLE, equal weights and a packed-pair variant
+ * PP_ACC_FP64FOLD, PP_POS_SINGLE, equal or per-particle weights and a
+ * packed-pair variant
  * (the default, or a PP_OPT_VARIANT override with interleaved staging), for
  * N <= 12288; PP_OPT_VARIANT otherwise still chooses the kernel of force
  * passes and of per-launch steps (set PP_RESIDENT_OFF to step with it).

@@ -705,7 +705,7 @@ ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
 {
     ResidentPlan rp;
     const int64_t limit = automatic ? kResidentAutoMaxN : kResidentMaxN;
-    if (c->n > limit || c->acc != PP_ACC_FP64FOLD || c->positions != PP_POS_SINGLE || c->wts ||
+    if (c->n > limit || c->acc != PP_ACC_FP64FOLD || c->positions != PP_POS_SINGLE ||
         stage_kind(c) != STAGE_F32I)
         return rp;
     static int coop = -1;
@@ -726,7 +726,7 @@ ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
     }
     const int threads = c->n >= kResidentWideN ? 512 : 256;
     int occ = 0;
-    if (resident_occupancy(c->npad, threads, &occ) != cudaSuccess || occ < 1) {
+    if (resident_occupancy(c->npad, threads, c->wrel != nullptr, &occ) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         return rp;
     }

@@ -71,7 +71,8 @@ struct ResidentArgs {
 // threads per CTA: 256 or 512 (the compiled instantiations)
 size_t resident_smem(int npad, int threads);
 cudaError_t resident_configure(int npad);
-cudaError_t resident_occupancy(int npad, int threads, int *blocks_per_sm);
+cudaError_t resident_occupancy(int npad, int threads, bool weighted, int *blocks_per_sm);
+// The weighted instantiation runs when a.wrel is set (per-particle weights).
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
                             cudaStream_t stream);
 

@@ -56,7 +56,8 @@ __device__ bool grid_sync_bounded(unsigned *bar, unsigned target, uint64_t limit
 // One component of the MODE_STEP epilogue (finish_particle, component-wise),
 // on state held in registers: a_{n+1} from the sum, Eq. G as staged, Eq. H,
 // and the staged coordinate of the next Eq. G.  Component 0 also writes the
-// weight slot (equal weights: 1).
+// weight slot (w_i / W with per-particle weights, else 1).
+template <bool W>
 __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c, double cc,
                                                double sum, double &r, double &v, double &a,
                                                void *dst)
@@ -70,10 +71,12 @@ __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c,
     const double rn = drift(r1, v1, an, p.dt, p.half_dt2);   // next Eq. G, staged only
     float *f = static_cast<float *>(dst) + 8 * (size_t)(i >> 1) + (i & 1);
     f[2 * c] = __double2float_rn(staged_coord(rn, cc, p.inv_l0));
-    if (c == 0) f[6] = 1.0f;
+    if (c == 0) f[6] = W ? p.wrel[i] : 1.0f;
 }
 
-template <int NT>
+// W: per-particle weights, each pair term multiplied by the source's staged
+// weight ratio w_j / W (one more f32x2 multiply per two pairs).
+template <int NT, bool W>
 __global__ void __launch_bounds__(NT, 1)
     force_resident_kernel(const ForceArgs p, const ResidentArgs ra)
 {
@@ -134,7 +137,8 @@ __global__ void __launch_bounds__(NT, 1)
                     float s0, s1;
                     f2_unpack(S, s0, s1);
                     const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
-                    const f2_t INV3 = f2_mul(f2_mul(INV, INV), INV);
+                    const f2_t INV3 = W ? f2_mul(f2_mul(f2_mul(INV, INV), INV), f2_pack(b.z, b.w))
+                                        : f2_mul(f2_mul(INV, INV), INV);
                     AX = f2_fma(INV3, DX, AX);
                     AY = f2_fma(INV3, DY, AY);
                     AZ = f2_fma(INV3, DZ, AZ);
@@ -158,7 +162,8 @@ __global__ void __launch_bounds__(NT, 1)
         if (owner) {
             double sum = 0.0;
             for (int k = 0; k < ra.q; ++k) sum += part[oc * NT + k * ra.bt + oti];   // fixed order
-            push_component(p, oi, oc, occ, sum, r_o, v_o, a_o, par ? ra.stage[0] : ra.stage[1]);
+            push_component<W>(p, oi, oc, occ, sum, r_o, v_o, a_o,
+                              par ? ra.stage[0] : ra.stage[1]);
         }
         if (s + 1 < ra.nsteps || p.skip_copy) {
             // test hook: CTA 0 withholds its first arrival, so every CTA's wait runs
@@ -178,10 +183,13 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-const void *resident_fn(int threads)
+const void *resident_fn(int threads, bool weighted)
 {
-    return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512>)
-                          : reinterpret_cast<const void *>(&force_resident_kernel<256>);
+    if (weighted)
+        return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512, true>)
+                              : reinterpret_cast<const void *>(&force_resident_kernel<256, true>);
+    return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512, false>)
+                          : reinterpret_cast<const void *>(&force_resident_kernel<256, false>);
 }
 
 }  // namespace
@@ -193,19 +201,20 @@ size_t resident_smem(int npad, int threads)
 
 cudaError_t resident_configure(int npad)
 {
-    for (int threads : {256, 512}) {
-        cudaError_t e = cudaFuncSetAttribute(resident_fn(threads),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)resident_smem(npad, threads));
-        if (e != cudaSuccess) return e;
-    }
+    for (int threads : {256, 512})
+        for (bool weighted : {false, true}) {
+            cudaError_t e = cudaFuncSetAttribute(resident_fn(threads, weighted),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)resident_smem(npad, threads));
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
-cudaError_t resident_occupancy(int npad, int threads, int *blocks_per_sm)
+cudaError_t resident_occupancy(int npad, int threads, bool weighted, int *blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, resident_fn(threads),
-                                                         threads, resident_smem(npad, threads));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, resident_fn(threads, weighted), threads, resident_smem(npad, threads));
 }
 
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
@@ -214,8 +223,9 @@ cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid
     ForceArgs ca = a;
     ResidentArgs cr = ra;
     void *args[] = {&ca, &cr};
-    return cudaLaunchCooperativeKernel(resident_fn(threads), dim3(grid), dim3(threads), args,
-                                       resident_smem(a.npad, threads), stream);
+    return cudaLaunchCooperativeKernel(resident_fn(threads, a.wrel != nullptr), dim3(grid),
+                                       dim3(threads), args, resident_smem(a.npad, threads),
+                                       stream);
 }
 
 }  // namespace ppk

@@ -104,6 +104,32 @@ def test_resident_is_bitwise_reproducible_across_call_grouping_and_checkpoints()
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("n", [700, 5000])
+def test_resident_weighted_run_matches_oracle_and_per_launch(n):
+    """Per-particle weights (each source term scaled by w_j / W): both CTA sizes, against
+    the oracle (which takes weights natively) and against the per-launch kernels."""
+    radius = 4e-6
+    pos = wl.uniform_sphere(n, radius, seed=960 + n)
+    w = 30.0 * (0.5 + 3.5 * wl.uniform(961 + n, 3, n))
+    eps = 1e-3 * radius
+    dt = dt_for(n, float(w.mean()), radius)
+    steps = 12
+    out = {}
+    for mode in (capi.PP_RESIDENT_AUTO, capi.PP_RESIDENT_OFF):
+        with capi.Simulation(n, 30.0, dt, eps) as sim:
+            sim.set_option(capi.PP_OPT_RESIDENT, mode)
+            sim.set_weights(w)
+            sim.load(pos)
+            assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == (mode == capi.PP_RESIDENT_AUTO)
+            sim.step(steps)
+            out[mode] = sim.state()[:3]
+    pr, vr, ar = oracle.vv_run(pos, np.zeros_like(pos), None, w, eps, dt, steps)
+    p, v, a = out[capi.PP_RESIDENT_AUTO]
+    assert rel(p - pos, pr - pos) <= TOL and rel(v, vr) <= TOL and rel(a, ar) <= TOL
+    for x, y in zip(out[capi.PP_RESIDENT_AUTO], out[capi.PP_RESIDENT_OFF]):
+        assert rel(x, y) <= TOL
+
+
 def test_resident_paper_lattice_without_softening():
     """The 16^3 cube lattice of Sec. 2.1 (eps = 0: the self pair is skipped by the floor on
     s, a coincident pair contributes zero), 20 steps of dt = 1e-13 s, against the oracle."""
@@ -139,7 +165,7 @@ def test_resident_selection_rules():
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # float4 staging
         sim.set_option(capi.PP_OPT_VARIANT, -1)
         sim.set_weights(np.full(3000, 1.0))
-        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # weighted form
         with pytest.raises(capi.PPError) as e:
             sim.set_option(capi.PP_OPT_RESIDENT, 3)
         assert e.value.status == capi.PP_ERR_ARG
