@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -199,24 +200,24 @@ bool cluster_fits(const Variant &v)
 int resident_ctas(const Variant &v)
 {
     static std::mutex lock;
-    static std::vector<int> cache;
-    int count = 0;
+    static std::map<std::pair<int, int>, int> cache;   // (device, variant) -> CTAs per SM
+    int count = 0, dev = 0;
     const Variant *vs = variants(&count);
     const int idx = (int)(&v - vs);
+    if (idx < 0 || idx >= count || cudaGetDevice(&dev) != cudaSuccess) return 1;
     std::lock_guard<std::mutex> g(lock);
-    if ((int)cache.size() < count) cache.assign(count, 0);
-    if (idx < 0 || idx >= count) return 1;
-    if (cache[idx] == 0) {
-        int occ = 0;
-        cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.T, v.smem) != cudaSuccess ||
-            occ < 1) {
-            cudaGetLastError();
-            occ = 1;
-        }
-        cache[idx] = occ;
+    auto it = cache.find({dev, idx});
+    if (it != cache.end()) return it->second;
+    int occ = 0;
+    // the attribute is per device and must be set before the occupancy query
+    cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.T, v.smem) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
     }
-    return cache[idx];
+    cache[{dev, idx}] = occ;
+    return occ;
 }
 
 struct Plan {
@@ -708,21 +709,17 @@ ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
     if (c->n > limit || c->acc != PP_ACC_FP64FOLD || c->positions != PP_POS_SINGLE ||
         stage_kind(c) != STAGE_F32I)
         return rp;
-    static int coop = -1;
-    if (coop < 0) {
-        int v = 0;
-        coop = cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, c->device) == cudaSuccess
-                   ? v
-                   : 0;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return rp;
     }
     if (!coop) return rp;
-    static bool configured = false;
-    if (!configured) {
-        if (resident_configure((int)round_up(kResidentMaxN, kPad)) != cudaSuccess) {
-            cudaGetLastError();
-            return rp;
-        }
-        configured = true;
+    static DeviceOnce configured;
+    if (configured.run(0, [] { return resident_configure((int)round_up(kResidentMaxN, kPad)); }) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return rp;
     }
     const int threads = c->n >= kResidentWideN ? 512 : 256;
     int occ = 0;

@@ -5,6 +5,9 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -44,6 +47,33 @@ struct Variant {
     size_t smem;  // dynamic shared memory bytes
     int cluster;  // CTAs per thread-block cluster (0: no cluster; the j-split is then S
                   // global-partial chunks chosen by the planner, else exactly `cluster`)
+};
+
+// One-time set-up per (device, key), e.g. a kernel's shared-memory attribute:
+// CUDA function attributes are per device, so the set-up runs once on every
+// device that uses the kernel.  Thread-safe; a failed set-up is retried.
+class DeviceOnce {
+public:
+    template <class F>
+    cudaError_t run(int key, F &&setup)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            if (done_.count({dev, key})) return cudaSuccess;
+        }
+        const cudaError_t e = setup();
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> g(mu_);
+            done_.insert({dev, key});
+        }
+        return e;
+    }
+
+private:
+    std::mutex mu_;
+    std::set<std::pair<int, int>> done_;
 };
 
 // Record the message pp_last_error() returns on this thread.

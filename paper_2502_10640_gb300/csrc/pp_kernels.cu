@@ -110,22 +110,20 @@ const Variant *variants(int *count)
 
 cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaStream_t stream)
 {
-    static bool configured[sizeof(kVariants) / sizeof(kVariants[0])] = {};
+    static DeviceOnce smem_attr, cluster_attr;
     const int idx = (int)(&v - kVariants);
-    if (idx >= 0 && idx < (int)(sizeof(kVariants) / sizeof(kVariants[0])) && !configured[idx]) {
-        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)v.smem);
-        if (e != cudaSuccess) return e;
-        configured[idx] = true;
-    }
+    cudaError_t e = smem_attr.run(idx, [&] {
+        return cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    });
+    if (e != cudaSuccess) return e;
     ForceArgs copy = a;
     void *args[] = {&copy};
     if (v.cluster <= 0) return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.T), args, v.smem, stream);
-    static bool cluster_configured[sizeof(kVariants) / sizeof(kVariants[0])] = {};
-    if (idx >= 0 && !cluster_configured[idx] && v.cluster > 8) {
-        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (v.cluster > 8) {
+        e = cluster_attr.run(idx, [&] {
+            return cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        });
         if (e != cudaSuccess) return e;
-        cluster_configured[idx] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
