@@ -202,7 +202,39 @@ def cpu_baseline(seconds: float, bunch=WORKLOAD):
     return {"value": m2 * n / el / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
             "kind": "oracle",
             "sample": f"FP64 oracle fields at {m2} of {n} particles against all {n} sources "
-                      f"({m2 * n:.3e} pairs, {el:.1f} s)"}
+                      f"({m2 * n:.3e} pairs, {el:.1f} s)",
+            "single_thread": single_thread_oracle(bunch)}
+
+
+def single_thread_oracle(bunch, targets: int = 512):
+    """The same oracle call on one host thread (a child process with OMP_NUM_THREADS=1):
+    `targets` sampled particles against all sources."""
+    import subprocess
+    import sys
+    code = ("import sys, time, numpy as np; sys.path.insert(0, sys.argv[1]); import oracle;"
+            "from paper_2502_10640_gb300 import workloads as wl;"
+            f"b = wl.WORKLOADS[{bunch_key(bunch)!r}]; pos = b.positions();"
+            f"idx = np.linspace(0, b.n - 1, {targets}).astype(np.int64);"
+            "oracle.fields_subset(pos, b.w, b.eps, idx[:8]);"
+            "t0 = time.perf_counter(); oracle.fields_subset(pos, b.w, b.eps, idx);"
+            "print(time.perf_counter() - t0)")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True,
+                             text=True, timeout=300, check=True)
+        el = float(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": str(e)[:200]}
+    return {"value": targets * bunch.n / el / 1e9, "unit": UNIT, "cores": 1,
+            "sample": f"{targets} of {bunch.n} particles against all {bunch.n} sources "
+                      f"({targets * bunch.n:.3e} pairs, {el:.2f} s)"}
+
+
+def bunch_key(bunch) -> str:
+    for k, v in wl.WORKLOADS.items():
+        if v is bunch:
+            return k
+    raise KeyError(bunch.name)
 
 
 def run_extras(sms: int, peak_tflops: float):
