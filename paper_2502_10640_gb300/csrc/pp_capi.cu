@@ -89,6 +89,9 @@ struct pp_ctx {
     uint64_t timeout_ns = 1000000000ull;
     int skip_copy = 0;
     int resident = PP_RESIDENT_AUTO;  // small-N stepping in one cooperative launch
+    bool res_plan_valid = false;      // cached resident plan and the settings it was made for
+    int64_t res_plan_key[6] = {};
+    alignas(8) unsigned char res_plan[64] = {};
 
     // cached step graphs for (graph_block, start parity)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -702,7 +705,7 @@ struct ResidentPlan {
 };
 
 // Can pp_step use the resident kernel, and how is the work split?
-ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
+ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
 {
     ResidentPlan rp;
     const int64_t limit = automatic ? kResidentAutoMaxN : kResidentMaxN;
@@ -740,6 +743,25 @@ ResidentPlan resident_plan(const pp_ctx *c, bool automatic)
     rp.chunk = (int)round_up(std::max((rp.nsrc + qmax - 1) / qmax, std::min(rp.nsrc, 32)), 2);
     rp.q = (rp.nsrc + rp.chunk - 1) / rp.chunk;
     rp.ok = true;
+    return rp;
+}
+
+// The plan depends only on settings that change between calls, so it is kept
+// with the key it was made for (no device queries on every pp_step).
+ResidentPlan resident_plan(pp_ctx *c, bool automatic)
+{
+    const int64_t key[6] = {c->acc, c->positions, c->wts != nullptr, c->variant_override,
+                            automatic, c->device};
+    if (c->res_plan_valid && std::equal(key, key + 6, c->res_plan_key)) {
+        ResidentPlan rp;
+        std::memcpy(&rp, c->res_plan, sizeof(rp));
+        return rp;
+    }
+    const ResidentPlan rp = compute_resident_plan(c, automatic);
+    static_assert(sizeof(ResidentPlan) <= sizeof(c->res_plan), "plan cache too small");
+    std::memcpy(c->res_plan, &rp, sizeof(rp));
+    std::copy(key, key + 6, c->res_plan_key);
+    c->res_plan_valid = true;
     return rp;
 }
 
@@ -970,7 +992,7 @@ pp_status pp_get_option(const pp_ctx *c, int key, int64_t *value)
     case PP_OPT_RESIDENT: *value = c->resident; return PP_OK;
     case PP_OPT_RESIDENT_ACTIVE:
         *value = (c->resident != PP_RESIDENT_OFF &&
-                  resident_plan(c, c->resident == PP_RESIDENT_AUTO).ok) ? 1 : 0;
+                  compute_resident_plan(c, c->resident == PP_RESIDENT_AUTO).ok) ? 1 : 0;
         return PP_OK;
     case PP_OPT_VARIANT: {
         int count = 0;
