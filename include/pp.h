@@ -355,8 +355,11 @@ typedef struct {
  * j-split count S and with S/4, S/2 and 2S, on the context's loaded particles, and
  * keep the fastest pair as the context's PP_OPT_VARIANT and PP_OPT_SPLIT.
  * Only force passes run (fields of the current positions into scratch): the
- * particle state and step counter are untouched.  Takes a few hundred force
- * passes at most; PP_ERR_STATE if no particles are loaded.  out may be NULL.
+ * particle state and step counter are untouched.  Where steps run on the
+ * resident small-N kernel (PP_OPT_RESIDENT), only variants with its staging
+ * layout are timed, so the choice keeps the steps resident.  Takes a few
+ * hundred force passes at most; PP_ERR_STATE if no particles are loaded.  out
+ * may be NULL.
  */
 pp_status pp_autotune(pp_ctx *ctx, pp_tune_result *out);
 

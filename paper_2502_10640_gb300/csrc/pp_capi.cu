@@ -1316,11 +1316,16 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
     int best_v = -1, best_s = 0, tried = 0;
     double best_ms = 1e300;
     pp_status st = PP_OK;
+    // where steps run on the resident small-N kernel, only variants with its staging
+    // layout are candidates, so that the choice does not take the steps off it
+    const bool keep_resident = c->resident != PP_RESIDENT_OFF &&
+                               compute_resident_plan(c, c->resident == PP_RESIDENT_AUTO).ok;
     for (int v = 0; v < count && st == PP_OK; ++v) {
         const bool split_layout = vs[v].stage == STAGE_F32X2 || vs[v].stage == STAGE_F32IX2;
         if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
             split_layout != (c->positions == PP_POS_SPLIT))
             continue;
+        if (keep_resident && vs[v].stage != STAGE_F32I) continue;
         if (vs[v].cluster > 0 && !cluster_fits(vs[v])) continue;   // cannot launch here
         c->variant_override = v;
         c->split_override = 0;

@@ -201,3 +201,22 @@ def test_resident_barrier_wait_reports_timeout_and_context_recovers(steps):
         p, v, a, step, _ = sim.state()
     pr, vr, ar = oracle.vv_run(pos, np.zeros_like(pos), None, 1.0, 1e-9, 1e-15, 3)
     assert step == 3 and rel(a, ar) <= TOL
+
+
+def test_autotune_keeps_small_n_steps_resident():
+    """At small N the autotuner only times variants whose staging layout the resident
+    kernel reads, so after tuning the steps still run resident and the results stay
+    within tolerance of the oracle."""
+    n = 1500
+    pos = wl.gaussian_bunch(n, 2e-6, seed=77)
+    dt = dt_for(n, 2.0, 2e-6)
+    with capi.Simulation(n, 2.0, dt, 1e-9) as sim:
+        sim.load(pos)
+        res = sim.autotune()
+        assert res["candidates"] >= 2
+        assert res["variant_name"].startswith(("f32x2.", "f32x2cl"))
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
+        sim.step(5)
+        a = sim.state()[2]
+    ar = oracle.vv_run(pos, np.zeros_like(pos), None, 2.0, 1e-9, dt, 5)[2]
+    assert rel(a, ar) <= TOL
