@@ -220,3 +220,18 @@ def test_autotune_keeps_small_n_steps_resident():
         a = sim.state()[2]
     ar = oracle.vv_run(pos, np.zeros_like(pos), None, 2.0, 1e-9, dt, 5)[2]
     assert rel(a, ar) <= TOL
+
+
+def test_resident_calls_longer_than_one_launch():
+    """A call of more steps than one cooperative launch takes (4096) is split into several
+    launches; the staging parity carries across them: 9000 steps in one call, in calls of
+    4500, and in calls of 1000 agree bitwise."""
+    n = 200
+    pos = wl.gaussian_bunch(n, 1e-6, seed=78)
+    dt = dt_for(n, 1.0, 1e-6, courant=0.002)
+    one = run(pos, None, 1.0, 1e-9, dt, 9000, capi.PP_RESIDENT_AUTO)
+    two = run(pos, None, 1.0, 1e-9, dt, 9000, capi.PP_RESIDENT_AUTO, chunks=[4500, 4500])
+    many = run(pos, None, 1.0, 1e-9, dt, 9000, capi.PP_RESIDENT_AUTO, chunks=[1000] * 9)
+    assert one[3] == 1
+    for x, y, z in zip(one[:3], two[:3], many[:3]):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
