@@ -91,6 +91,7 @@ struct pp_batch {
     unsigned *d_queue = nullptr;
     int *d_err = nullptr;             // [0] wait ran out, [1] non-finite input
     double *mom_partials = nullptr, *mom_out = nullptr, *mom_host = nullptr;
+    int *err_host = nullptr;          // pinned copy of the error word
     bool dirty = true;
     int graph_block = 16;
     cudaGraphExec_t graph = nullptr;
@@ -171,8 +172,11 @@ pp_status launch_batch(pp_batch *b, const BunchDesc *descs, const BatchHeader *h
 
 pp_status read_errors(pp_batch *b, int *flags)
 {
-    B_CUDA(cudaMemcpyAsync(flags, b->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(cudaMemcpyAsync(b->err_host, b->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
     B_CUDA(cudaStreamSynchronize(b->stream));
+    flags[0] = b->err_host[0];
+    flags[1] = b->err_host[1];
     if (flags[0] || flags[1]) B_CUDA(cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int), b->stream));
     return PP_OK;
 }
@@ -334,6 +338,7 @@ pp_status pp_batch_destroy(pp_batch *b)
     cudaFree(b->mom_partials);
     cudaFree(b->mom_out);
     if (b->mom_host) cudaFreeHost(b->mom_host);
+    if (b->err_host) cudaFreeHost(b->err_host);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
     return PP_OK;
@@ -376,7 +381,8 @@ pp_status pp_batch_create(int64_t budget_bytes, pp_batch **out)
                     cudaMalloc(&b->d_err, 2 * sizeof(int)) == cudaSuccess &&
                     cudaMalloc(&b->mom_partials, kMomBlocks * kMomSlots * sizeof(double)) == cudaSuccess &&
                     cudaMalloc(&b->mom_out, kMomSlots * sizeof(double)) == cudaSuccess &&
-                    cudaMallocHost(&b->mom_host, kMomSlots * sizeof(double)) == cudaSuccess;
+                    cudaMallocHost(&b->mom_host, kMomSlots * sizeof(double)) == cudaSuccess &&
+                    cudaMallocHost(&b->err_host, 2 * sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return bail(PP_ERR_NOMEM, "device allocation failed");

@@ -73,6 +73,7 @@ struct pp_ctx {
     int *err = nullptr;            // [0]: wait ran out, [1]: non-finite input,
                                    // [2]: grid-barrier counter of the resident kernel
     double *mom_host = nullptr;    // pinned
+    int *err_host = nullptr;       // pinned copy of err[0..1], read after each synchronisation
 
     int parity = 0;
     bool loaded = false;
@@ -349,8 +350,8 @@ ForceArgs base_args(const pp_ctx *c, const Plan &pl, int mode, const void *src, 
 // Read and clear the device error word; maps it to a status.
 pp_status check_device_errors(pp_ctx *c, bool reset_state_on_timeout)
 {
-    int h[2] = {0, 0};
-    PP_CUDA(cudaMemcpyAsync(h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    int *h = c->err_host;
+    PP_CUDA(cudaMemcpyAsync(h, c->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PP_CUDA(cudaStreamSynchronize(c->stream));
     if (h[0]) {
         PP_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->stream));
@@ -518,11 +519,12 @@ pp_status export_aos(pp_ctx *c, double *const src[3], double *out, int kind)
 
 pp_status take_bad_input_flag(pp_ctx *c, bool *bad)
 {
-    int h = 0;
-    PP_CUDA(cudaMemcpyAsync(&h, c->err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int *h = c->err_host + 1;
+    PP_CUDA(cudaMemcpyAsync(h, c->err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PP_CUDA(cudaStreamSynchronize(c->stream));
-    if (h) PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
-    *bad = h != 0;
+    const bool set = *h != 0;
+    if (set) PP_CUDA(cudaMemsetAsync(c->err + 1, 0, sizeof(int), c->stream));
+    *bad = set;
     return PP_OK;
 }
 
@@ -837,6 +839,7 @@ pp_status pp_destroy(pp_ctx *c)
     cudaFree(c->mom_out);
     cudaFree(c->err);
     if (c->mom_host) cudaFreeHost(c->mom_host);
+    if (c->err_host) cudaFreeHost(c->err_host);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
     return PP_OK;
@@ -883,7 +886,8 @@ pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **o
                cudaMalloc(&c->mom_partials, kMomBlocks * kMomSlots * sizeof(double)) == cudaSuccess &&
                cudaMalloc(&c->mom_out, kMomSlots * sizeof(double)) == cudaSuccess &&
                cudaMalloc(&c->err, 4 * sizeof(int)) == cudaSuccess &&
-               cudaMallocHost(&c->mom_host, kMomSlots * sizeof(double)) == cudaSuccess;
+               cudaMallocHost(&c->mom_host, kMomSlots * sizeof(double)) == cudaSuccess &&
+               cudaMallocHost(&c->err_host, 4 * sizeof(int)) == cudaSuccess;
     if (!okm) {
         cudaGetLastError();
         return bail(PP_ERR_NOMEM, "device allocation failed");
