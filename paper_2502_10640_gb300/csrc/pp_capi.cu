@@ -689,8 +689,10 @@ pp_status decide_positions(pp_ctx *c)
 
 // ---- resident small-N stepping ------------------------------------------------
 // Largest N whose staged sources fit one CTA's shared memory alongside the
-// partial sums (npad = 12288: 192 KB + 12 KB).
+// partial sums (npad = 12288: 192 KB + 12 KB); hi/lo staging needs twice the
+// bytes per source.
 constexpr int64_t kResidentMaxN = 12288;
+constexpr int64_t kResidentMaxNSplit = 6144;
 // Largest N for PP_RESIDENT_AUTO.  Measured on GB300 the resident kernel is
 // faster than the per-launch kernels at every N up to the fit limit (2.9x at
 // N = 64, 1.8x at 4096, 1.3x at 12288), so the two limits coincide.
@@ -702,7 +704,7 @@ constexpr int64_t kResidentWideN = 3072;
 constexpr int64_t kResidentMaxSteps = 4096;
 
 struct ResidentPlan {
-    bool ok = false;
+    bool ok = false, split = false;
     int grid = 0, threads = 0, bt = 0, q = 0, chunk = 0, nsrc = 0;
 };
 
@@ -710,9 +712,11 @@ struct ResidentPlan {
 ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
 {
     ResidentPlan rp;
-    const int64_t limit = automatic ? kResidentAutoMaxN : kResidentMaxN;
-    if (c->n > limit || c->acc != PP_ACC_FP64FOLD || c->positions != PP_POS_SINGLE ||
-        stage_kind(c) != STAGE_F32I)
+    const bool split = c->positions == PP_POS_SPLIT;
+    const int64_t limit = split ? kResidentMaxNSplit
+                                : (automatic ? kResidentAutoMaxN : kResidentMaxN);
+    if (c->n > limit || c->acc != PP_ACC_FP64FOLD ||
+        stage_kind(c) != (split ? STAGE_F32IX2 : STAGE_F32I))
         return rp;
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) != cudaSuccess) {
@@ -721,18 +725,22 @@ ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
     }
     if (!coop) return rp;
     static DeviceOnce configured;
-    if (configured.run(0, [] { return resident_configure((int)round_up(kResidentMaxN, kPad)); }) !=
-        cudaSuccess) {
+    if (configured.run(0, [] {
+            return resident_configure((int)round_up(kResidentMaxN, kPad),
+                                      (int)round_up(kResidentMaxNSplit, kPad));
+        }) != cudaSuccess) {
         cudaGetLastError();
         return rp;
     }
     const int threads = c->n >= kResidentWideN ? 512 : 256;
     int occ = 0;
-    if (resident_occupancy(c->npad, threads, c->wrel != nullptr, &occ) != cudaSuccess || occ < 1) {
+    if (resident_occupancy(c->npad, threads, c->wrel != nullptr, split, &occ) != cudaSuccess ||
+        occ < 1) {
         cudaGetLastError();
         return rp;
     }
     rp.threads = threads;
+    rp.split = split;
     // one CTA per SM at most, and at least 8 targets per CTA
     const int64_t g0 = std::min<int64_t>((int64_t)c->sms, std::max<int64_t>(1, (c->n + 7) / 8));
     rp.bt = (int)((c->n + g0 - 1) / g0);
@@ -788,7 +796,7 @@ pp_status step_resident(pp_ctx *c, const ResidentPlan &rp, int64_t nsteps)
         ra.parity0 = c->parity;
         ra.nsteps = k;
         PP_CUDA(cudaMemsetAsync(ra.bar, 0, sizeof(unsigned), c->stream));
-        PP_CUDA(launch_resident(a, ra, rp.grid, rp.threads, c->stream));
+        PP_CUDA(launch_resident(a, ra, rp.grid, rp.threads, rp.split, c->stream));
         a.skip_copy = 0;
         c->parity ^= (k & 1);
         left -= k;
@@ -1329,7 +1337,9 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
         if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
             split_layout != (c->positions == PP_POS_SPLIT))
             continue;
-        if (keep_resident && vs[v].stage != STAGE_F32I) continue;
+        if (keep_resident &&
+            vs[v].stage != (c->positions == PP_POS_SPLIT ? STAGE_F32IX2 : STAGE_F32I))
+            continue;
         if (vs[v].cluster > 0 && !cluster_fits(vs[v])) continue;   // cannot launch here
         c->variant_override = v;
         c->split_override = 0;

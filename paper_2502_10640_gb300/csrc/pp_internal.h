@@ -89,7 +89,7 @@ cudaError_t launch_variant(const Variant &v, const ForceArgs &a, int grid, cudaS
 // launch (pp_resident.cu).  The staged source array lives in each CTA's
 // shared memory.
 struct ResidentArgs {
-    void *stage[2];   // ping-pong staging (STAGE_F32I), npad entries each
+    void *stage[2];   // ping-pong staging (STAGE_F32I or STAGE_F32IX2), npad entries each
     int parity0;      // buffer holding the staged r_{n+1} at the first step
     int nsteps;
     int bt;           // targets per CTA (grid = ceil(n / bt))
@@ -98,13 +98,15 @@ struct ResidentArgs {
     int nsrc;         // sources summed: n rounded up to even (the odd tail is padding)
     unsigned *bar;    // grid-barrier arrival counter, zero at launch
 };
-// threads per CTA: 256 or 512 (the compiled instantiations)
-size_t resident_smem(int npad, int threads);
-cudaError_t resident_configure(int npad);
-cudaError_t resident_occupancy(int npad, int threads, bool weighted, int *blocks_per_sm);
-// The weighted instantiation runs when a.wrel is set (per-particle weights).
+// threads per CTA: 256 or 512 (the compiled instantiations); split: hi/lo
+// staging (STAGE_F32IX2, both parts in shared memory); the weighted form runs
+// when a.wrel is set (per-particle weights, single staging only).
+size_t resident_smem(int npad, int threads, bool split);
+cudaError_t resident_configure(int npad_single, int npad_split);
+cudaError_t resident_occupancy(int npad, int threads, bool weighted, bool split,
+                               int *blocks_per_sm);
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
-                            cudaStream_t stream);
+                            bool split, cudaStream_t stream);
 
 // Deterministic O(N) kernels.
 // AoS [n][3] -> three SoA arrays; sets *bad to 1 if any input is not finite.

@@ -55,9 +55,10 @@ __device__ bool grid_sync_bounded(unsigned *bar, unsigned target, uint64_t limit
 
 // One component of the MODE_STEP epilogue (finish_particle, component-wise),
 // on state held in registers: a_{n+1} from the sum, Eq. G as staged, Eq. H,
-// and the staged coordinate of the next Eq. G.  Component 0 also writes the
-// weight slot (w_i / W with per-particle weights, else 1).
-template <bool W>
+// and the staged coordinate of the next Eq. G (with SPLIT its hi and lo
+// parts).  Component 0 also writes the weight slot (w_i / W with per-particle
+// weights, else 1).
+template <bool W, bool SPLIT>
 __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c, double cc,
                                                double sum, double &r, double &v, double &a,
                                                void *dst)
@@ -70,20 +71,31 @@ __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c,
     a = an;
     const double rn = drift(r1, v1, an, p.dt, p.half_dt2);   // next Eq. G, staged only
     float *f = static_cast<float *>(dst) + 8 * (size_t)(i >> 1) + (i & 1);
-    f[2 * c] = __double2float_rn(staged_coord(rn, cc, p.inv_l0));
+    const double pc = staged_coord(rn, cc, p.inv_l0);
+    const float hi = __double2float_rn(pc);
+    f[2 * c] = hi;
     if (c == 0) f[6] = W ? p.wrel[i] : 1.0f;
+    if (SPLIT) {   // lo parts in the same layout, 4 npad floats further on
+        float *fl = f + 4 * (size_t)p.npad;
+        fl[2 * c] = __double2float_rn(pc - (double)hi);
+        if (c == 0) fl[6] = 0.0f;
+    }
 }
 
 // W: per-particle weights, each pair term multiplied by the source's staged
 // weight ratio w_j / W (one more f32x2 multiply per two pairs).
-template <int NT, bool W>
+// SPLIT: hi/lo staged positions (STAGE_F32IX2): shared memory holds both
+// parts, and each separation is (hi_i - hi_j) + (lo_i - lo_j).
+template <int NT, bool W, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1)
     force_resident_kernel(const ForceArgs p, const ResidentArgs ra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sj4 = reinterpret_cast<float4 *>(smem_raw);   // staged sources, interleaved pairs
     const float *sj = reinterpret_cast<const float *>(smem_raw);
-    double *part = reinterpret_cast<double *>(smem_raw + (size_t)p.npad * sizeof(float4));
+    constexpr int NPARTS = SPLIT ? 2 : 1;                  // hi (and lo) copies, npad each
+    double *part =
+        reinterpret_cast<double *>(smem_raw + (size_t)NPARTS * p.npad * sizeof(float4));
     __shared__ int s_flag;
 
     const int tid = threadIdx.x;
@@ -117,12 +129,18 @@ __global__ void __launch_bounds__(NT, 1)
         // other CTAs wrote these entries during the previous step: read through L2
         const float4 *src = static_cast<const float4 *>(par ? ra.stage[1] : ra.stage[0]);
         for (int k = tid; k < ra.nsrc; k += NT) sj4[k] = __ldcg(src + k);
+        if (SPLIT)
+            for (int k = tid; k < ra.nsrc; k += NT) sj4[p.npad + k] = __ldcg(src + p.npad + k);
         __syncthreads();
 
         double sx = 0.0, sy = 0.0, sz = 0.0;
         if (work) {
             const float *q = sj + 8 * (i >> 1) + (i & 1);
             const f2_t X = f2_pack(q[0], q[0]), Y = f2_pack(q[2], q[2]), Z = f2_pack(q[4], q[4]);
+            const float *ql = q + 4 * (size_t)p.npad;
+            const f2_t XL = SPLIT ? f2_pack(ql[0], ql[0]) : 0ull;
+            const f2_t YL = SPLIT ? f2_pack(ql[2], ql[2]) : 0ull;
+            const f2_t ZL = SPLIT ? f2_pack(ql[4], ql[4]) : 0ull;
             for (int t0 = j0; t0 < j1; t0 += kResFold) {
                 const int t1 = min(t0 + kResFold, j1);
                 f2_t AX = 0ull, AY = 0ull, AZ = 0ull;
@@ -130,9 +148,15 @@ __global__ void __launch_bounds__(NT, 1)
                 for (int j = t0; j < t1; j += 2) {
                     const float4 a = sj4[j];       // x_j x_j+1 y_j y_j+1
                     const float4 b = sj4[j + 1];   // z_j z_j+1 w_j w_j+1
-                    const f2_t DX = f2_sub(X, f2_pack(a.x, a.y));
-                    const f2_t DY = f2_sub(Y, f2_pack(a.z, a.w));
-                    const f2_t DZ = f2_sub(Z, f2_pack(b.x, b.y));
+                    f2_t DX = f2_sub(X, f2_pack(a.x, a.y));
+                    f2_t DY = f2_sub(Y, f2_pack(a.z, a.w));
+                    f2_t DZ = f2_sub(Z, f2_pack(b.x, b.y));
+                    if (SPLIT) {
+                        const float4 al = sj4[p.npad + j], bl = sj4[p.npad + j + 1];
+                        DX = f2_add(DX, f2_sub(XL, f2_pack(al.x, al.y)));
+                        DY = f2_add(DY, f2_sub(YL, f2_pack(al.z, al.w)));
+                        DZ = f2_add(DZ, f2_sub(ZL, f2_pack(bl.x, bl.y)));
+                    }
                     const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
                     float s0, s1;
                     f2_unpack(S, s0, s1);
@@ -162,8 +186,8 @@ __global__ void __launch_bounds__(NT, 1)
         if (owner) {
             double sum = 0.0;
             for (int k = 0; k < ra.q; ++k) sum += part[oc * NT + k * ra.bt + oti];   // fixed order
-            push_component<W>(p, oi, oc, occ, sum, r_o, v_o, a_o,
-                              par ? ra.stage[0] : ra.stage[1]);
+            push_component<W, SPLIT>(p, oi, oc, occ, sum, r_o, v_o, a_o,
+                                     par ? ra.stage[0] : ra.stage[1]);
         }
         if (s + 1 < ra.nsteps || p.skip_copy) {
             // test hook: CTA 0 withholds its first arrival, so every CTA's wait runs
@@ -183,48 +207,58 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-const void *resident_fn(int threads, bool weighted)
+template <int NT>
+const void *resident_fn_nt(bool weighted, bool split)
 {
-    if (weighted)
-        return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512, true>)
-                              : reinterpret_cast<const void *>(&force_resident_kernel<256, true>);
-    return threads == 512 ? reinterpret_cast<const void *>(&force_resident_kernel<512, false>)
-                          : reinterpret_cast<const void *>(&force_resident_kernel<256, false>);
+    if (split) return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, true>);
+    return weighted ? reinterpret_cast<const void *>(&force_resident_kernel<NT, true, false>)
+                    : reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false>);
+}
+
+// (per-particle weights with split positions is not a mode of the library)
+const void *resident_fn(int threads, bool weighted, bool split)
+{
+    return threads == 512 ? resident_fn_nt<512>(weighted, split)
+                          : resident_fn_nt<256>(weighted, split);
 }
 
 }  // namespace
 
-size_t resident_smem(int npad, int threads)
+size_t resident_smem(int npad, int threads, bool split)
 {
-    return (size_t)npad * sizeof(float4) + 3 * (size_t)threads * sizeof(double);
+    return (size_t)(split ? 2 : 1) * npad * sizeof(float4) + 3 * (size_t)threads * sizeof(double);
 }
 
-cudaError_t resident_configure(int npad)
+cudaError_t resident_configure(int npad_single, int npad_split)
 {
     for (int threads : {256, 512})
-        for (bool weighted : {false, true}) {
-            cudaError_t e = cudaFuncSetAttribute(resident_fn(threads, weighted),
+        for (int form = 0; form < 3; ++form) {
+            const bool weighted = form == 1, split = form == 2;
+            const int npad = split ? npad_split : npad_single;
+            cudaError_t e = cudaFuncSetAttribute(resident_fn(threads, weighted, split),
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)resident_smem(npad, threads));
+                                                 (int)resident_smem(npad, threads, split));
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
 }
 
-cudaError_t resident_occupancy(int npad, int threads, bool weighted, int *blocks_per_sm)
+cudaError_t resident_occupancy(int npad, int threads, bool weighted, bool split,
+                               int *blocks_per_sm)
 {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, resident_fn(threads, weighted), threads, resident_smem(npad, threads));
+        blocks_per_sm, resident_fn(threads, weighted, split), threads,
+        resident_smem(npad, threads, split));
 }
 
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
-                            cudaStream_t stream)
+                            bool split, cudaStream_t stream)
 {
     ForceArgs ca = a;
     ResidentArgs cr = ra;
     void *args[] = {&ca, &cr};
-    return cudaLaunchCooperativeKernel(resident_fn(threads, a.wrel != nullptr), dim3(grid),
-                                       dim3(threads), args, resident_smem(a.npad, threads),
+    return cudaLaunchCooperativeKernel(resident_fn(threads, a.wrel != nullptr, split), dim3(grid),
+                                       dim3(threads), args, resident_smem(a.npad, threads, split),
                                        stream);
 }
 

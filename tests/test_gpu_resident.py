@@ -130,6 +130,28 @@ def test_resident_weighted_run_matches_oracle_and_per_launch(n):
         assert rel(x, y) <= TOL
 
 
+@pytest.mark.parametrize("n", [1500, 4099, 6144])
+def test_resident_split_positions_on_close_pairs(n):
+    """Hi/lo staging in the resident kernel (both CTA sizes, up to the largest N whose
+    two staged copies fit shared memory): on a 1 nm-softened ball whose closest pairs sit
+    ~1e3 times closer than its radius, where single FP32 staging loses ~3e-5, the run
+    stays within 1e-5 of the oracle."""
+    radius, w, eps = 20e-6, 10.0, 1e-9
+    pos = wl.uniform_sphere(n, radius, seed=7 + n)
+    dt = dt_for(n, w, radius)
+    steps = 4
+    with capi.Simulation(n, w, dt, eps, positions=capi.PP_POS_SPLIT) as sim:
+        sim.load(pos)
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
+        sim.step(steps)
+        p, v, a, step, _ = sim.state()
+    pr, vr, ar = oracle.vv_run(pos, np.zeros_like(pos), None, w, eps, dt, steps)
+    assert step == steps
+    assert rel(a, ar) <= TOL
+    assert rel(v, vr) <= TOL
+    assert rel(p - pos, pr - pos) <= TOL
+
+
 def test_resident_paper_lattice_without_softening():
     """The 16^3 cube lattice of Sec. 2.1 (eps = 0: the self pair is skipped by the floor on
     s, a coincident pair contributes zero), 20 steps of dt = 1e-13 s, against the oracle."""
@@ -157,7 +179,7 @@ def test_resident_selection_rules():
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
         sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_FP64FOLD)
         sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SPLIT)
-        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # hi/lo form
         sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SINGLE)
         sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index("f32x2.fold64.t64r1k128"))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # same staging
@@ -172,6 +194,9 @@ def test_resident_selection_rules():
     with capi.Simulation(12288, 1.0, 1e-15, 1e-9) as sim:
         sim.load(wl.gaussian_bunch(12288, 2e-6, seed=74))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # the largest that fits
+    with capi.Simulation(6145, 1.0, 1e-15, 1e-9, positions=capi.PP_POS_SPLIT) as sim:
+        sim.load(wl.gaussian_bunch(6145, 2e-6, seed=79))
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # hi/lo does not fit
     with capi.Simulation(12289, 1.0, 1e-15, 1e-9) as sim:
         sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_ON)
         sim.load(wl.gaussian_bunch(12289, 2e-6, seed=75))
