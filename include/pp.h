@@ -123,10 +123,12 @@ enum {
  * floors s = |d|^2 + eps^2 at 1e-24 in staged units (L0^2), so the self pair
  * adds exactly 0 without a test per pair; for separations the FP32 staging
  * resolves this changes s by less than one FP32 rounding.  Applicable with
- * PP_ACC_FP64FOLD and a packed-pair variant (the default, or a PP_OPT_VARIANT
- * override with interleaved staging): with PP_POS_SINGLE (equal or
- * per-particle weights) for N <= 12288, with PP_POS_SPLIT (hi/lo staging,
- * both parts in shared memory) for N <= 6144.  PP_OPT_VARIANT otherwise
+ * the FP32 pair paths (PP_ACC_FP64FOLD or PP_ACC_KAHAN, whose form folds a
+ * thread's tile partials into a compensated FP32 pair) and a packed-pair
+ * variant (the default, or a PP_OPT_VARIANT override with interleaved
+ * staging): with PP_POS_SINGLE (equal or per-particle weights) for
+ * N <= 12288, with PP_POS_SPLIT (hi/lo staging, both parts in shared memory)
+ * for N <= 6144.  PP_OPT_VARIANT otherwise
  * still chooses the kernel of force passes and of per-launch steps (set
  * PP_RESIDENT_OFF to step with it).
  * Results differ from the per-launch kernels' at the FP32 rounding level

@@ -704,8 +704,8 @@ constexpr int64_t kResidentWideN = 3072;
 constexpr int64_t kResidentMaxSteps = 4096;
 
 struct ResidentPlan {
-    bool ok = false, split = false;
-    int grid = 0, threads = 0, bt = 0, q = 0, chunk = 0, nsrc = 0;
+    bool ok = false;
+    int form = 0, grid = 0, threads = 0, bt = 0, q = 0, chunk = 0, nsrc = 0;
 };
 
 // Can pp_step use the resident kernel, and how is the work split?
@@ -715,9 +715,12 @@ ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
     const bool split = c->positions == PP_POS_SPLIT;
     const int64_t limit = split ? kResidentMaxNSplit
                                 : (automatic ? kResidentAutoMaxN : kResidentMaxN);
-    if (c->n > limit || c->acc != PP_ACC_FP64FOLD ||
+    if (c->n > limit || c->acc == PP_ACC_FP64_FULL ||
         stage_kind(c) != (split ? STAGE_F32IX2 : STAGE_F32I))
         return rp;
+    // the library's modes exclude weights or Kahan with split positions, and weights with Kahan
+    const int form = split ? RES_SPLIT
+                           : c->acc == PP_ACC_KAHAN ? RES_KAHAN : c->wrel ? RES_WEIGHTED : RES_PLAIN;
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -734,13 +737,12 @@ ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
     }
     const int threads = c->n >= kResidentWideN ? 512 : 256;
     int occ = 0;
-    if (resident_occupancy(c->npad, threads, c->wrel != nullptr, split, &occ) != cudaSuccess ||
-        occ < 1) {
+    if (resident_occupancy(c->npad, threads, form, &occ) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         return rp;
     }
     rp.threads = threads;
-    rp.split = split;
+    rp.form = form;
     // one CTA per SM at most, and at least 8 targets per CTA
     const int64_t g0 = std::min<int64_t>((int64_t)c->sms, std::max<int64_t>(1, (c->n + 7) / 8));
     rp.bt = (int)((c->n + g0 - 1) / g0);
@@ -796,7 +798,7 @@ pp_status step_resident(pp_ctx *c, const ResidentPlan &rp, int64_t nsteps)
         ra.parity0 = c->parity;
         ra.nsteps = k;
         PP_CUDA(cudaMemsetAsync(ra.bar, 0, sizeof(unsigned), c->stream));
-        PP_CUDA(launch_resident(a, ra, rp.grid, rp.threads, rp.split, c->stream));
+        PP_CUDA(launch_resident(a, ra, rp.grid, rp.threads, rp.form, c->stream));
         a.skip_copy = 0;
         c->parity ^= (k & 1);
         left -= k;

@@ -98,15 +98,15 @@ struct ResidentArgs {
     int nsrc;         // sources summed: n rounded up to even (the odd tail is padding)
     unsigned *bar;    // grid-barrier arrival counter, zero at launch
 };
-// threads per CTA: 256 or 512 (the compiled instantiations); split: hi/lo
-// staging (STAGE_F32IX2, both parts in shared memory); the weighted form runs
-// when a.wrel is set (per-particle weights, single staging only).
-size_t resident_smem(int npad, int threads, bool split);
+// threads per CTA: 256 or 512 (the compiled instantiations).  Forms: plain
+// (single staging, equal weights, FP64 fold), per-particle weights, hi/lo
+// staging (STAGE_F32IX2, both parts in shared memory), compensated FP32 fold.
+enum ResidentForm : int { RES_PLAIN = 0, RES_WEIGHTED = 1, RES_SPLIT = 2, RES_KAHAN = 3 };
+size_t resident_smem(int npad, int threads, int form);
 cudaError_t resident_configure(int npad_single, int npad_split);
-cudaError_t resident_occupancy(int npad, int threads, bool weighted, bool split,
-                               int *blocks_per_sm);
+cudaError_t resident_occupancy(int npad, int threads, int form, int *blocks_per_sm);
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
-                            bool split, cudaStream_t stream);
+                            int form, cudaStream_t stream);
 
 // Deterministic O(N) kernels.
 // AoS [n][3] -> three SoA arrays; sets *bad to 1 if any input is not finite.

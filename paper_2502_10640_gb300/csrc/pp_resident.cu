@@ -86,7 +86,10 @@ __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c,
 // weight ratio w_j / W (one more f32x2 multiply per two pairs).
 // SPLIT: hi/lo staged positions (STAGE_F32IX2): shared memory holds both
 // parts, and each separation is (hi_i - hi_j) + (lo_i - lo_j).
-template <int NT, bool W, bool SPLIT>
+// KAHAN (PP_ACC_KAHAN): a thread folds its FP32 tile partials into a
+// compensated FP32 pair (TwoSum) instead of FP64; the threads' pairs are
+// then added in FP64 in the fixed order, like the FP64-fold form.
+template <int NT, bool W, bool SPLIT, bool KAHAN = false>
 __global__ void __launch_bounds__(NT, 1)
     force_resident_kernel(const ForceArgs p, const ResidentArgs ra)
 {
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
 
         double sx = 0.0, sy = 0.0, sz = 0.0;
+        float kh[3] = {0.f, 0.f, 0.f}, kl[3] = {0.f, 0.f, 0.f};   // KAHAN: hi, lo per component
         if (work) {
             const float *q = sj + 8 * (i >> 1) + (i & 1);
             const f2_t X = f2_pack(q[0], q[0]), Y = f2_pack(q[2], q[2]), Z = f2_pack(q[4], q[4]);
@@ -171,9 +175,25 @@ __global__ void __launch_bounds__(NT, 1)
                 f2_unpack(AX, x0, x1);
                 f2_unpack(AY, y0, y1);
                 f2_unpack(AZ, z0, z1);
-                sx += (double)(x0 + x1);
-                sy += (double)(y0 + y1);
-                sz += (double)(z0 + z1);
+                if (KAHAN) {
+                    const float f[3] = {x0 + x1, y0 + y1, z0 + z1};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float hs, e;
+                        two_sum(kh[c], f[c], hs, e);
+                        kh[c] = hs;
+                        kl[c] = __fadd_rn(kl[c], e);
+                    }
+                } else {
+                    sx += (double)(x0 + x1);
+                    sy += (double)(y0 + y1);
+                    sz += (double)(z0 + z1);
+                }
+            }
+            if (KAHAN) {
+                sx = (double)kh[0] + (double)kl[0];
+                sy = (double)kh[1] + (double)kl[1];
+                sz = (double)kh[2] + (double)kl[2];
             }
         }
         part[tid] = sx;
@@ -208,58 +228,58 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 template <int NT>
-const void *resident_fn_nt(bool weighted, bool split)
+const void *resident_fn_nt(int form)
 {
-    if (split) return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, true>);
-    return weighted ? reinterpret_cast<const void *>(&force_resident_kernel<NT, true, false>)
-                    : reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false>);
+    switch (form) {
+    case RES_WEIGHTED: return reinterpret_cast<const void *>(&force_resident_kernel<NT, true, false>);
+    case RES_SPLIT: return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, true>);
+    case RES_KAHAN:
+        return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false, true>);
+    default: return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false>);
+    }
 }
 
-// (per-particle weights with split positions is not a mode of the library)
-const void *resident_fn(int threads, bool weighted, bool split)
+const void *resident_fn(int threads, int form)
 {
-    return threads == 512 ? resident_fn_nt<512>(weighted, split)
-                          : resident_fn_nt<256>(weighted, split);
+    return threads == 512 ? resident_fn_nt<512>(form) : resident_fn_nt<256>(form);
 }
 
 }  // namespace
 
-size_t resident_smem(int npad, int threads, bool split)
+size_t resident_smem(int npad, int threads, int form)
 {
-    return (size_t)(split ? 2 : 1) * npad * sizeof(float4) + 3 * (size_t)threads * sizeof(double);
+    return (size_t)(form == RES_SPLIT ? 2 : 1) * npad * sizeof(float4) +
+           3 * (size_t)threads * sizeof(double);
 }
 
 cudaError_t resident_configure(int npad_single, int npad_split)
 {
     for (int threads : {256, 512})
-        for (int form = 0; form < 3; ++form) {
-            const bool weighted = form == 1, split = form == 2;
-            const int npad = split ? npad_split : npad_single;
-            cudaError_t e = cudaFuncSetAttribute(resident_fn(threads, weighted, split),
+        for (int form : {RES_PLAIN, RES_WEIGHTED, RES_SPLIT, RES_KAHAN}) {
+            const int npad = form == RES_SPLIT ? npad_split : npad_single;
+            cudaError_t e = cudaFuncSetAttribute(resident_fn(threads, form),
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)resident_smem(npad, threads, split));
+                                                 (int)resident_smem(npad, threads, form));
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
 }
 
-cudaError_t resident_occupancy(int npad, int threads, bool weighted, bool split,
-                               int *blocks_per_sm)
+cudaError_t resident_occupancy(int npad, int threads, int form, int *blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, resident_fn(threads, weighted, split), threads,
-        resident_smem(npad, threads, split));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, resident_fn(threads, form),
+                                                         threads,
+                                                         resident_smem(npad, threads, form));
 }
 
 cudaError_t launch_resident(const ForceArgs &a, const ResidentArgs &ra, int grid, int threads,
-                            bool split, cudaStream_t stream)
+                            int form, cudaStream_t stream)
 {
     ForceArgs ca = a;
     ResidentArgs cr = ra;
     void *args[] = {&ca, &cr};
-    return cudaLaunchCooperativeKernel(resident_fn(threads, a.wrel != nullptr, split), dim3(grid),
-                                       dim3(threads), args, resident_smem(a.npad, threads, split),
-                                       stream);
+    return cudaLaunchCooperativeKernel(resident_fn(threads, form), dim3(grid), dim3(threads), args,
+                                       resident_smem(a.npad, threads, form), stream);
 }
 
 }  // namespace ppk

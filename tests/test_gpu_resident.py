@@ -152,6 +152,39 @@ def test_resident_split_positions_on_close_pairs(n):
     assert rel(p - pos, pr - pos) <= TOL
 
 
+def test_resident_compensated_fold():
+    """PP_ACC_KAHAN on the resident kernel: a thread's tile partials go into a compensated
+    FP32 pair.  With one tile per thread (N = 3000) that pair is the tile partial itself,
+    so the run is bitwise the FP64-fold run; with four tiles per thread (N = 12288) both
+    stay within 1e-5 of the oracle's fields and agree with each other to 1e-12."""
+    n = 3000
+    pos = wl.gaussian_bunch(n, 2e-6, seed=80)
+    dt = dt_for(n, 2.0, 2e-6)
+    out = {}
+    for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN):
+        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc) as sim:
+            sim.load(pos)
+            assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
+            sim.step(7)
+            out[acc] = sim.state()[:3]
+    for x, y in zip(out[capi.PP_ACC_FP64FOLD], out[capi.PP_ACC_KAHAN]):
+        assert np.array_equal(x, y)
+    n = 12288
+    pos = wl.gaussian_bunch(n, 3e-6, seed=81)
+    dt = dt_for(n, 2.0, 3e-6)
+    acc_out = {}
+    for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN):
+        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc) as sim:
+            sim.load(pos)
+            assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
+            sim.step(2)
+            acc_out[acc] = sim.state()[2]
+    ar = oracle.vv_run(pos, np.zeros_like(pos), None, 2.0, 1e-9, dt, 2)[2]
+    for acc, a in acc_out.items():
+        assert rel(a, ar) <= TOL, acc
+    assert rel(acc_out[capi.PP_ACC_KAHAN], acc_out[capi.PP_ACC_FP64FOLD]) <= 1e-12
+
+
 def test_resident_paper_lattice_without_softening():
     """The 16^3 cube lattice of Sec. 2.1 (eps = 0: the self pair is skipped by the floor on
     s, a coincident pair contributes zero), 20 steps of dt = 1e-13 s, against the oracle."""
@@ -176,7 +209,9 @@ def test_resident_selection_rules():
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
         sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_AUTO)
         sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_KAHAN)
-        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # compensated form
+        sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_FP64_FULL)
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # FP64 pair math
         sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_FP64FOLD)
         sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SPLIT)
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # hi/lo form
