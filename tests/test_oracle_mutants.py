@@ -31,9 +31,16 @@ MUTANTS = [
     ("emittance centred", "double x = pos[3 * i + 0];", "double x = pos[3 * i + 0] - cx;", 0),
     ("emittance cross term dropped", "double e2 = mx2 * mvx2 - mxvx * mxvx;", "double e2 = mx2 * mvx2;", 0),
     ("momentum without weight", "px += m * vx;", "px += OR_ME * vx;", 0),
+    ("last source skipped", "for (int64_t j = 0; j < N; ++j) {\n            if (j == i) continue;\n            double dx",
+     "for (int64_t j = 0; j < N - 1; ++j) {\n            if (j == i) continue;\n            double dx", 0),
+    ("z separation from the source's y", "double dz = pos[3 * i + 2] - pos[3 * j + 2];",
+     "double dz = pos[3 * i + 2] - pos[3 * j + 1];", 0),
+    ("softening not squared", "const double eps2 = eps * eps;", "const double eps2 = eps;", 0),
 ]
 
 PIN_CALLS = [
+    (pins.test_brute_force_exact_fields_small_n, {"n": 17, "eps_frac": 0.0}),
+    (pins.test_brute_force_exact_fields_small_n, {"n": 64, "eps_frac": 0.3}),
     (pins.test_two_body_acceleration_closed_form, {"eps": 0.0}),
     (pins.test_two_body_acceleration_closed_form, {"eps": 0.3e-6}),
     (pins.test_ring_on_axis_field, {}),

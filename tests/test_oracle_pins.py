@@ -112,6 +112,65 @@ def test_shell_theorem_exterior_point():
     assert math.hypot(a[0], a[2]) < 0.01 * expect
 
 
+# --- fields: brute force in exact arithmetic ------------------------------------------------
+
+def _exact_fields(pos, w, eps, k, qe):
+    """Eq. B / Eq. E recomputed without rounding error in the geometry: every double is
+    taken as the exact rational it represents, the separations and s = |d|^2 + eps^2 are
+    exact fractions, and only s^(3/2) and the quotient are rounded, in 60-digit decimal
+    arithmetic (correctly rounded square root).  Returns the field [N][3] and, per
+    component, sum_j |Q_j d / s^(3/2)| (the scale of the summation error bound)."""
+    import decimal
+    from fractions import Fraction
+    ctx = decimal.Context(prec=60)
+    dec = lambda f: ctx.divide(decimal.Decimal(f.numerator), decimal.Decimal(f.denominator))
+    n = pos.shape[0]
+    P = [[Fraction(float(x)) for x in row] for row in pos]
+    W = [Fraction(float(x)) for x in np.broadcast_to(w, (n,))]
+    e2 = Fraction(float(eps)) ** 2
+    kq = dec(Fraction(float(k)) * Fraction(float(qe)))
+    E = np.zeros((n, 3))
+    S = np.zeros((n, 3))
+    for i in range(n):
+        acc = [decimal.Decimal(0)] * 3
+        mag = [decimal.Decimal(0)] * 3
+        for j in range(n):
+            if j == i:
+                continue
+            d = [P[i][c] - P[j][c] for c in range(3)]
+            s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + e2
+            if s == 0:
+                continue
+            sd = dec(s)
+            s32 = ctx.multiply(sd, sd.sqrt(ctx))
+            for c in range(3):
+                t = ctx.divide(dec(W[j] * d[c]), s32)
+                acc[c] = ctx.add(acc[c], t)
+                mag[c] = ctx.add(mag[c], abs(t))
+        for c in range(3):
+            E[i, c] = float(ctx.multiply(kq, acc[c]))
+            S[i, c] = float(abs(ctx.multiply(kq, mag[c])))
+    return E, S
+
+
+@pytest.mark.parametrize("n", [2, 5, 17, 64])
+@pytest.mark.parametrize("eps_frac", [0.0, 0.3])
+def test_brute_force_exact_fields_small_n(n, eps_frac):
+    """Random clouds of N <= 64 with random weights: the oracle's field equals the field
+    recomputed in exact arithmetic to the FP64 rounding of its own sum (per element within
+    the recursive-summation bound 4 (N + 4) u sum_j |term|, and 1e-14 in relative L2)."""
+    sigma = 2e-6
+    pos = wl.gaussian_bunch(n, sigma, seed=500 + n)
+    w = 1.0 + 4.0 * wl.uniform(500 + n, 9, n)
+    eps = eps_frac * sigma
+    c = oracle.constants()
+    E = oracle.fields(pos, w, eps)
+    ref, scale = _exact_fields(pos, w, eps, c["k"], -c["e"])
+    u = 2.0 ** -53
+    assert np.all(np.abs(E - ref) <= 4 * (n + 4) * u * scale + 1e-300)
+    assert rel(E, ref) <= 1e-14
+
+
 # --- fields: invariants ------------------------------------------------------------------
 
 def _random_cloud(n, seed, scale=5e-6):
