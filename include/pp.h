@@ -81,18 +81,25 @@ typedef enum {
 /* How staged source positions carry precision into the FP32 pair math
  * (option PP_OPT_POSITIONS).  SINGLE rounds each staged coordinate to one
  * float, so a separation d carries an absolute error of about 2^-24 |r|,
- * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs.  SPLIT
- * stages hi + lo floats (about 48 bits) and forms d = (hi_i - hi_j) +
+ * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs (random
+ * balls of ~1e4 particles with 1 nm softening reach 3e-5 in relative L2).
+ * SPLIT stages hi + lo floats (about 48 bits) and forms d = (hi_i - hi_j) +
  * (lo_i - lo_j), exact in its hi part for close pairs, at six more FP32
- * operations per pair.  SPLIT is available with PP_ACC_FP64FOLD.  AUTO
- * decides at every pp_load_particles: it computes the fields once with each
- * staging and keeps SPLIT if the two differ by more than 5e-6 in relative L2
- * (the single-staging error on that input), SINGLE otherwise (two extra force
- * passes at load; pp_get_option reports the choice). */
+ * operations per pair (about 30 % slower).  SPLIT works with every FP32 pair
+ * path (FP64 fold, compensated fold, per-particle weights).
+ * AUTO, the default, decides whenever the library picks a staging frame
+ * (pp_load_particles, pp_set_weights on a loaded context, pp_set_state
+ * without a frame): it computes the fields once with each staging and keeps
+ * SPLIT if the two differ by more than 5e-6 in relative L2 (the
+ * single-staging error on that input, half the 1e-5 field tolerance), SINGLE
+ * otherwise.  That costs two extra force passes at those calls only; steps
+ * run at the speed of the staging chosen.  pp_get_option(PP_OPT_POSITIONS)
+ * reports the staging in force, PP_OPT_POSITIONS_AUTO whether AUTO is on.
+ * With PP_ACC_FP64_FULL sources are FP64 and the setting has no effect. */
 typedef enum {
-    PP_POS_SINGLE = 0,    /* default */
+    PP_POS_SINGLE = 0,
     PP_POS_SPLIT = 1,
-    PP_POS_AUTO = 2
+    PP_POS_AUTO = 2       /* default */
 } pp_positions;
 
 /* Option keys for pp_set_option. */
@@ -107,6 +114,7 @@ enum {
     PP_OPT_POSITIONS = 7,      /* value: a pp_positions (FP32 pair paths only)                 */
     PP_OPT_RESIDENT = 8,       /* value: a pp_resident (small-N stepping)                      */
     PP_OPT_RESIDENT_ACTIVE = 9,/* pp_get_option only: 1 if pp_step now runs the resident kernel */
+    PP_OPT_POSITIONS_AUTO = 10,/* pp_get_option only: 1 if PP_POS_AUTO decides the staging     */
     PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy (the
                                   resident kernel: one grid-barrier arrival), so its bounded
                                   waits expire and the call returns PP_ERR_TIMEOUT (tests the
@@ -126,9 +134,9 @@ enum {
  * the FP32 pair paths (PP_ACC_FP64FOLD or PP_ACC_KAHAN, whose form folds a
  * thread's tile partials into a compensated FP32 pair) and a packed-pair
  * variant (the default, or a PP_OPT_VARIANT override with interleaved
- * staging): with PP_POS_SINGLE (equal or per-particle weights) for
- * N <= 12288, with PP_POS_SPLIT (hi/lo staging, both parts in shared memory)
- * for N <= 6144.  PP_OPT_VARIANT otherwise
+ * staging): with single staging (equal or per-particle weights) for
+ * N <= 12288, with hi/lo staging (FP64 fold and equal weights; both parts in
+ * shared memory) for N <= 6144.  PP_OPT_VARIANT otherwise
  * still chooses the kernel of force passes and of per-launch steps (set
  * PP_RESIDENT_OFF to step with it).
  * Results differ from the per-launch kernels' at the FP32 rounding level
@@ -173,9 +181,9 @@ pp_status pp_load_particles(pp_ctx *ctx, const double *pos, const double *vel, i
  * weight of pp_create, which stays the reference weight W: sources enter the
  * sum with w_j (staged as the FP32 ratio w_j / W), and KE, PE and momentum use
  * w_i.  w = NULL returns to equal weights.  If particles are loaded, a is
- * recomputed for the new weights (the state stays at the same time).  Needs
- * PP_ACC_FP64FOLD (or PP_ACC_FP64_FULL) with single positions, else
- * PP_ERR_ARG.  The paper uses one weight for all macro-particles (Sec. 2.1);
+ * recomputed for the new weights (the state stays at the same time; with
+ * PP_POS_AUTO the staging is decided again first).  Needs PP_ACC_FP64FOLD (or
+ * PP_ACC_FP64_FULL), else PP_ERR_ARG; either staging of positions.  The paper uses one weight for all macro-particles (Sec. 2.1);
  * this generalises it.
  */
 pp_status pp_set_weights(pp_ctx *ctx, const double *w, int on_device);
@@ -222,15 +230,20 @@ pp_status pp_get_particles(pp_ctx *ctx, double *pos, double *vel, int on_device)
 /*
  * Checkpoint / resume.  pp_get_state copies r, v, a ([N][3] each; any may be
  * NULL), the step counter and the staging frame out; pp_set_state restores
- * them exactly (no force pass).  The staging frame is 4 host doubles
- * {cx, cy, cz, L0}: the centre and the power-of-two length about which
- * positions are staged to FP32.  Passing the frame saved by pp_get_state makes
- * stepping on from the restored state bitwise identical to stepping on
- * without the round trip; frame = NULL chooses a fresh frame (centroid and
- * RMS radius of pos), which changes results at the FP32 rounding level only.
- * acc must be the acceleration that belongs to pos (as pp_get_state returns
- * it).  Invalid frame (non-finite, L0 <= 0 or not a power of two) -> PP_ERR_ARG.
+ * them exactly (no force pass).  The staging frame is PP_FRAME_LEN = 5 host
+ * doubles {cx, cy, cz, L0, staging}: the centre and the power-of-two length
+ * about which positions are staged to FP32, and the staging in force
+ * (PP_POS_SINGLE or PP_POS_SPLIT).  A context in PP_POS_AUTO adopts the saved
+ * staging; a context with an explicit positions mode keeps its own.  Passing
+ * the frame saved by pp_get_state makes stepping on from the restored state
+ * bitwise identical to stepping on without the round trip; frame = NULL
+ * chooses a fresh frame (centroid and RMS radius of pos, and under
+ * PP_POS_AUTO a fresh staging decision), which changes results at the FP32
+ * rounding level only.  acc must be the acceleration that belongs to pos (as
+ * pp_get_state returns it).  Invalid frame (non-finite, L0 <= 0 or not a
+ * power of two, staging not 0 or 1) -> PP_ERR_ARG.
  */
+#define PP_FRAME_LEN 5
 pp_status pp_get_state(pp_ctx *ctx, double *pos, double *vel, double *acc, int64_t *step,
                        double *frame, int on_device);
 pp_status pp_set_state(pp_ctx *ctx, const double *pos, const double *vel, const double *acc,
@@ -252,22 +265,28 @@ pp_status pp_check_mapped(const void *p, int64_t bytes);
  * softening eps at positions pos, written to E_out; both are [N][3] device
  * memory of the current CUDA device, read and written on `stream` (a
  * cudaStream_t, or NULL for the legacy default stream).  No context needed.
+ * Sources are staged hi/lo (about 48-bit separations, the PP_POS_SPLIT
+ * arithmetic), so the result meets the 1e-5 relative-L2 field tolerance also
+ * on inputs with very close pairs.
  *
  * It allocates nothing, for callers that may not call cudaMalloc (code that
  * runs inside a memory arena owned by a host framework, code that must not
  * trigger the allocator's implicit synchronisation, plug-ins restricted to the
  * buffers they are handed).  Every intermediate lives in one fixed device
- * array of about 3.8 MB that each GPU loading this library holds until the
+ * array of 4.09 MB that each GPU loading this library holds until the
  * process exits; N above PP_FIELDS_NOALLOC_MAX_N returns PP_ERR_ARG.
  *
  * All calls on a device share that array and it keeps the last call's
  * contents (the call clears what must start at zero itself).  Calls whose work
  * overlaps on the GPU race on it: serialise them.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress with that
- * device current); make that first call before any stream capture.  The call
- * synchronises `stream` before it returns.  Errors: PP_ERR_ARG (size, null
- * pointer, non-finite input), PP_ERR_TIMEOUT, PP_ERR_CUDA; message via
- * pp_last_error(NULL).
+ * device current); make that first call before any stream capture.  The
+ * lookup is repeated if the device's context has been recreated since (after
+ * cudaDeviceReset, for instance).  The call synchronises `stream` three times
+ * before it returns: twice mid-call, to read the centroid and RMS radius that
+ * fix the staging frame, and once at the end, to read the error word.
+ * Errors: PP_ERR_ARG (size, null pointer, non-finite input), PP_ERR_TIMEOUT,
+ * PP_ERR_CUDA; message via pp_last_error(NULL).
  */
 #define PP_FIELDS_NOALLOC_MAX_N 16384
 pp_status pp_fields_noalloc(int64_t N, double w, double softening, const double *pos,

@@ -38,10 +38,12 @@ PP_OPT_VARIANT = 6
 PP_OPT_POSITIONS = 7
 PP_OPT_RESIDENT = 8
 PP_OPT_RESIDENT_ACTIVE = 9
+PP_OPT_POSITIONS_AUTO = 10
 
 PP_POS_SINGLE = 0
 PP_POS_SPLIT = 1
 PP_POS_AUTO = 2
+PP_FRAME_LEN = 5
 PP_OPT_TEST_SKIP_COPY = 99
 
 PP_RESIDENT_OFF = 0
@@ -305,7 +307,7 @@ def pp_get_particles(ctx, pos=None, vel=None):
 
 
 def pp_get_state(ctx, pos=None, vel=None, acc=None):
-    """(pos, vel, acc, step, frame); frame = (cx, cy, cz, L0) of the FP32 staging."""
+    """(pos, vel, acc, step, frame); frame = (cx, cy, cz, L0, staging) of the FP32 staging."""
     n = pp_get_n(ctx)
     if pos is None and vel is None and acc is None:
         pos, vel, acc = (np.empty((n, 3)) for _ in range(3))
@@ -314,7 +316,7 @@ def pp_get_state(ctx, pos=None, vel=None, acc=None):
     a, oa, k3 = _arg(acc, n, True)
     on = _same_kind(*(o for o, x in ((op, pos), (ov, vel), (oa, acc)) if x is not None))
     step = _I64()
-    frame = (ctypes.c_double * 4)()
+    frame = (ctypes.c_double * PP_FRAME_LEN)()
     _check(load().pp_get_state(ctx, p, v, a, ctypes.byref(step), frame, on), ctx)
     return pos, vel, acc, step.value, tuple(frame)
 
@@ -325,7 +327,9 @@ def pp_set_state(ctx, pos, vel, acc, step: int, frame=None) -> None:
     v, ov, k2 = _arg(vel, n, False)
     a, oa, k3 = _arg(acc, n, False)
     on = _same_kind(op, ov, oa)
-    fr = None if frame is None else (ctypes.c_double * 4)(*[float(x) for x in frame])
+    if frame is not None and len(frame) != PP_FRAME_LEN:
+        raise ValueError(f"frame must hold {PP_FRAME_LEN} values (cx, cy, cz, L0, staging)")
+    fr = None if frame is None else (ctypes.c_double * PP_FRAME_LEN)(*[float(x) for x in frame])
     _check(load().pp_set_state(ctx, p, v, a, int(step), fr, on), ctx)
 
 
@@ -358,9 +362,15 @@ def pp_fields_noalloc(n: int, w: float, softening: float, pos, out, stream=None)
         if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
                 and tuple(x.shape) == (n, 3)):
             raise ValueError("pos and out must be contiguous CUDA float64 tensors of shape (n, 3)")
+    if out.device != pos.device:
+        raise ValueError(f"pos is on {pos.device} but out is on {out.device}")
     s = stream if stream is not None else torch.cuda.current_stream(pos.device)
-    _check(load().pp_fields_noalloc(int(n), float(w), float(softening), pos.data_ptr(),
-                                     out.data_ptr(), s.cuda_stream))
+    if s.device != pos.device:
+        raise ValueError(f"the stream belongs to {s.device}, the tensors to {pos.device}")
+    # the library works on the current device: make it the tensors' device
+    with torch.cuda.device(pos.device):
+        _check(load().pp_fields_noalloc(int(n), float(w), float(softening), pos.data_ptr(),
+                                         out.data_ptr(), s.cuda_stream))
 
 
 def pp_last_error(ctx=None) -> str:

@@ -82,7 +82,7 @@ struct pp_ctx {
 
     int acc = PP_ACC_FP64FOLD;
     int positions = PP_POS_SINGLE;   // in force: SINGLE or SPLIT
-    bool positions_auto = false;     // decide SINGLE or SPLIT at every load
+    bool positions_auto = true;      // PP_POS_AUTO (the default): decide at every load
     double auto_rel = -1.0;          // last AUTO estimate of the single-staging error
     int split_override = 0;
     int variant_override = -1;
@@ -118,7 +118,8 @@ const Variant *variant_by_name(const char *want)
     const Variant *vs = variants(&count);
     for (int i = 0; i < count; ++i)
         if (std::strcmp(vs[i].name, want) == 0) return &vs[i];
-    return &vs[0];
+    std::fprintf(stderr, "pp: no kernel variant named %s\n", want);
+    std::abort();   // a missing table entry is a build error, not a runtime condition
 }
 
 // The variant that runs this context's force passes: the override if it fits
@@ -135,10 +136,20 @@ const Variant *force_variant(const pp_ctx *c)
         if (v.kind == want_kind && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
             return &v;
     }
+    if (c->wts && c->positions == PP_POS_SPLIT) {  // weights on hi/lo staged sources
+        if (c->n >= 32768) return variant_by_name("f32x2wsplit.sfold64.t128r2k512m4");
+        if (c->n >= 8192) return variant_by_name("f32x2wsplit.sfold64.t128r4k256m4");
+        return variant_by_name("f32x2wsplit.fold64.t64r1k128");
+    }
     if (c->wts) {  // per-particle weights: packed kernels that read the weight lanes
         if (c->n >= 32768) return variant_by_name("f32x2w.sfold64.t128r4k512m4");
         if (c->n >= 8192) return variant_by_name("f32x2w.fold64.t128r2k128");
         return variant_by_name("f32x2w.fold64.t64r1k128");
+    }
+    if (c->positions == PP_POS_SPLIT && c->acc == PP_ACC_KAHAN) {
+        if (c->n >= 32768) return variant_by_name("f32x2split.kahan.st128r2k512m4");
+        if (c->n >= 8192) return variant_by_name("f32x2split.kahan.st128r4k256m4");
+        return variant_by_name("f32x2split.kahan.t64r1k128");
     }
     if (c->positions == PP_POS_SPLIT) {
         if (c->n >= 32768) return variant_by_name("f32x2split.sfold64.t128r2k512m4");
@@ -641,6 +652,7 @@ __global__ void __launch_bounds__(kDiffThreads)
 // half the 1e-5 tolerance, so single staging is kept only with a 2x margin.
 pp_status decide_positions(pp_ctx *c)
 {
+    if (f64_pairs(c)) return PP_OK;   // FP64 sources: nothing to choose
     const size_t bytes = (size_t)c->n * 3 * sizeof(double);
     double *e_split = nullptr, *parts = nullptr;
     if (cudaMalloc(&e_split, bytes) != cudaSuccess ||
@@ -649,7 +661,7 @@ pp_status decide_positions(pp_ctx *c)
         cudaFree(e_split);
         return fail(PP_ERR_NOMEM, "cannot allocate the positions-mode check");
     }
-    void *scratch = c->stage[1];
+    void *scratch = c->stage[c->parity ^ 1];
     pp_status st = PP_OK;
     double h[2 * kDiffBlocks];
     c->positions = PP_POS_SINGLE;
@@ -718,7 +730,9 @@ ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
     if (c->n > limit || c->acc == PP_ACC_FP64_FULL ||
         stage_kind(c) != (split ? STAGE_F32IX2 : STAGE_F32I))
         return rp;
-    // the library's modes exclude weights or Kahan with split positions, and weights with Kahan
+    // hi/lo staging runs resident with the FP64 fold and equal weights only (weights
+    // with the compensated fold are excluded by the library's modes)
+    if (split && (c->acc == PP_ACC_KAHAN || c->wrel)) return rp;
     const int form = split ? RES_SPLIT
                            : c->acc == PP_ACC_KAHAN ? RES_KAHAN : c->wrel ? RES_WEIGHTED : RES_PLAIN;
     int coop = 0;
@@ -930,13 +944,9 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
         const bool new_auto = key == PP_OPT_POSITIONS ? value == PP_POS_AUTO : c->positions_auto;
         const int new_pos = key == PP_OPT_POSITIONS ? (value == PP_POS_AUTO ? c->positions : (int)value)
                                                     : c->positions;
-        if (new_auto && (new_acc != PP_ACC_FP64FOLD || c->wts))
-            return fail(PP_ERR_ARG, "automatic positions need PP_ACC_FP64FOLD and equal weights");
+        if (c->wts && new_acc == PP_ACC_KAHAN)
+            return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL");
         c->positions_auto = new_auto;
-        if (new_pos == PP_POS_SPLIT && new_acc == PP_ACC_KAHAN)
-            return fail(PP_ERR_ARG, "split positions are implemented with the FP64 fold only");
-        if (c->wts && (new_pos == PP_POS_SPLIT || new_acc == PP_ACC_KAHAN))
-            return fail(PP_ERR_ARG, "per-particle weights need the FP64 fold and single positions");
         const int old_kind = stage_kind(c);
         c->acc = new_acc;
         c->positions = new_pos;
@@ -999,6 +1009,7 @@ pp_status pp_get_option(const pp_ctx *c, int key, int64_t *value)
     switch (key) {
     case PP_OPT_ACC: *value = c->acc; return PP_OK;
     case PP_OPT_POSITIONS: *value = c->positions; return PP_OK;
+    case PP_OPT_POSITIONS_AUTO: *value = c->positions_auto ? 1 : 0; return PP_OK;
     case PP_OPT_STREAM: *value = (int64_t)reinterpret_cast<intptr_t>(c->stream); return PP_OK;
     case PP_OPT_SPLIT: *value = c->split_override; return PP_OK;
     case PP_OPT_GRAPH_BLOCK: *value = c->graph_block; return PP_OK;
@@ -1067,9 +1078,8 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
     if (pp_status s = check_ctx(c)) return s;
     PP_CUDA(cudaSetDevice(c->device));
     if (!valid_mem(on_device)) return fail(PP_ERR_ARG, "bad memory kind");
-    if (c->acc == PP_ACC_KAHAN || c->positions == PP_POS_SPLIT)
-        return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL "
-                                "with single positions");
+    if (c->acc == PP_ACC_KAHAN)
+        return fail(PP_ERR_ARG, "per-particle weights need PP_ACC_FP64FOLD or PP_ACC_FP64_FULL");
     if (!w) {
         cudaFree(c->wts);
         cudaFree(c->wrel);
@@ -1108,7 +1118,14 @@ pp_status pp_set_weights(pp_ctx *c, const double *w, int on_device)
     drop_graphs(c);
     if (!c->loaded) return PP_OK;
     // the acceleration belongs to the weights: recompute a(r) and restage r_{n+1}
-    pp_status st = pad_both(c);
+    // (PP_POS_AUTO first decides the staging again for the weighted sum)
+    pp_status st = PP_OK;
+    if (c->positions_auto) {
+        st = pad_both(c);
+        if (st == PP_OK) st = decide_positions(c);
+        if (st != PP_OK) return st;
+    }
+    st = pad_both(c);
     if (st == PP_OK) st = stage_current(c, c->stage[c->parity ^ 1], stage_kind(c));
     if (st == PP_OK)
         st = force_pass(c, MODE_INIT, c->stage[c->parity ^ 1], c->stage[c->parity], nullptr);
@@ -1129,11 +1146,16 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
             return fail(PP_ERR_ARG, "invalid staging frame");
         int e = 0;
         if (std::frexp(frame[3], &e) != 0.5) return fail(PP_ERR_ARG, "frame scale must be a power of two");
+        if (frame[4] != (double)PP_POS_SINGLE && frame[4] != (double)PP_POS_SPLIT)
+            return fail(PP_ERR_ARG, "frame staging must be PP_POS_SINGLE or PP_POS_SPLIT");
     }
     PP_CUDA(cudaSetDevice(c->device));
     drop_graphs(c);
     c->loaded = false;
     bool bad = false;
+    // PP_POS_AUTO resumes with the staging the saved run used (bitwise resume); an
+    // explicit positions mode of this context is kept as it is
+    if (frame && c->positions_auto && !f64_pairs(c)) c->positions = (int)frame[4];
     if (frame && on_device != PP_MEM_HOST) {
         // device or mapped host buffers: one pass converts the state, checks it and
         // stages r_{n+1} = Eq. G(r_n, v_n, a_n); one synchronisation
@@ -1185,6 +1207,11 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
         st = choose_frame(c);
         if (st != PP_OK) return st;
         c->parity = 0;
+        if (c->positions_auto) {   // a fresh frame: decide the staging for these positions
+            st = pad_both(c);
+            if (st == PP_OK) st = decide_positions(c);
+            if (st != PP_OK) return st;
+        }
         st = restage_pending(c);
         if (st != PP_OK) return st;
     }
@@ -1235,6 +1262,7 @@ pp_status pp_get_state(pp_ctx *c, double *pos, double *vel, double *acc, int64_t
         frame[1] = c->cy;
         frame[2] = c->cz;
         frame[3] = c->l0;
+        frame[4] = (double)c->positions;
     }
     PP_CUDA(cudaStreamSynchronize(c->stream));
     return PP_OK;

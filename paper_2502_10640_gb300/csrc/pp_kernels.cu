@@ -90,6 +90,14 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 4, true, false, true>("f32x2split.sfold64.t128r2k512m4"),
     make_f32x2<128, 4, 256, 3, 4, true, false, true>("f32x2split.sfold64.t128r4k256m4"),
     make_f32x2<64, 1, 128, 4, 8, false, false, true>("f32x2split.fold64.t64r1k128"),
+    // hi/lo split positions with the compensated FP32 fold
+    make_f32x2<128, 2, 512, 3, 4, true, false, true, 2, true>("f32x2split.kahan.st128r2k512m4"),
+    make_f32x2<128, 4, 256, 3, 4, true, false, true, 2, true>("f32x2split.kahan.st128r4k256m4"),
+    make_f32x2<64, 1, 128, 4, 8, false, false, true, 2, true>("f32x2split.kahan.t64r1k128"),
+    // hi/lo split positions with per-particle weights (FP64 fold)
+    make_f32x2<128, 2, 512, 3, 4, true, true, true>("f32x2wsplit.sfold64.t128r2k512m4"),
+    make_f32x2<128, 4, 256, 3, 4, true, true, true>("f32x2wsplit.sfold64.t128r4k256m4"),
+    make_f32x2<64, 1, 128, 4, 8, false, true, true>("f32x2wsplit.fold64.t64r1k128"),
     // per-particle weights (sources scaled by w_j / W)
     make_f32x2<128, 4, 512, 3, 4, true, true>("f32x2w.sfold64.t128r4k512m4"),
     make_f32x2<128, 2, 128, 4, 4, false, true>("f32x2w.fold64.t128r2k128"),

@@ -1,17 +1,22 @@
 // pp_noalloc.cu -- pp_fields_noalloc: the field of Eq. B for callers that
 // cannot allocate device memory.
 //
+// Sources are staged hi/lo (two floats per coordinate, about 48 significant
+// bits), so close pairs keep their separations and the field meets the 1e-5
+// relative-L2 tolerance also on inputs whose closest pairs sit 1e3 times closer
+// than the bunch size (single FP32 staging loses ~3e-5 there).
+//
 // Some callers cannot call cudaMalloc at all: code that runs inside a
 // memory pool or arena owned by a host framework that forbids foreign
 // allocations, code that must never trigger the allocator's implicit device
 // synchronisation in a latency-critical loop, or a plug-in that may only use
 // the buffers it is handed.  This entry point serves them.  It takes device
 // inputs and outputs from the caller and keeps every intermediate (SoA copy of
-// the positions, staged float4 sources, j-split partial sums, tickets, moment
-// partials, error word) in one file-scope __device__ array of fixed size.
+// the positions, staged hi/lo float4 sources, j-split partial sums, tickets,
+// moment partials, error word) in one file-scope __device__ array of fixed size.
 //
 // The array exists on every GPU that loads this library, for the lifetime of
-// the process (kScratchBytes, about 3.8 MB).  All calls on a device share it
+// the process (kScratchBytes, 4.09 MB).  All calls on a device share it
 // and it keeps the last call's contents; the entry point clears the parts that
 // must start at zero (tickets, error word) on every call.  Calls whose work
 // overlaps on the GPU (several host threads, or several streams) race on the
@@ -19,12 +24,17 @@
 //
 // The host-side name of a __device__ array is only a stand-in for it, not a
 // device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture.
+// cudaGetSymbolAddress (with that device current) and caches it together with
+// the identity of the device's current context; make that first call before any
+// stream capture.  If the context was destroyed and recreated since (for
+// example after cudaDeviceReset), the next call sees another context identity
+// and looks the address up again instead of writing through a stale one.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/pp.h"
 #include "pp_internal.h"
@@ -43,8 +53,8 @@ constexpr int kMaxNib = (kNoAllocMaxN + kBI - 1) / kBI;
 // Byte offsets of the parts of the scratch array (each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffSoa = 0;                                              // 3 x double[max_pad]
-constexpr size_t kOffStage = align256(kOffSoa + 3 * sizeof(double) * kMaxPad);  // float4[max_pad]
-constexpr size_t kOffPartial = align256(kOffStage + sizeof(float4) * kMaxPad);
+constexpr size_t kOffStage = align256(kOffSoa + 3 * sizeof(double) * kMaxPad);  // float4[2 max_pad]
+constexpr size_t kOffPartial = align256(kOffStage + 2 * sizeof(float4) * kMaxPad);
 constexpr size_t kOffTickets =
     align256(kOffPartial + sizeof(double) * kNoAllocMaxSplit * 3 * (size_t)kMaxNib * kBI);
 constexpr size_t kOffMomPart = align256(kOffTickets + sizeof(unsigned) * kMaxNib);
@@ -57,6 +67,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_lock;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context identity of each address
 
 // Errors are reported through pp_last_error(), like every other call.
 pp_status na_fail(pp_status s, const char *m)
@@ -79,16 +90,46 @@ pp_status na_cuda(cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return na_cuda(e_, #call);  \
     } while (0)
 
-// Device address of the scratch array on the current device (looked up once).
+// Identity of the calling thread's current CUDA context (unique for the life of
+// the process; a context recreated after a device reset gets a new one), or 0
+// where the driver does not report one.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static const std::pair<GetCurrent, GetId> fns = [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+            a = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            b = nullptr;
+        return std::make_pair(reinterpret_cast<GetCurrent>(a), reinterpret_cast<GetId>(b));
+    }();
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!fns.first || !fns.second || fns.first(&ctx) != CUDA_SUCCESS || !ctx ||
+        fns.second(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: looked up once
+// per device (with that device current), and again if the device's context
+// has been recreated since.
 pp_status scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return na_fail(PP_ERR_ARG, "device ordinal out of range");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> g(g_setup_lock);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return na_cuda(e, "cudaGetSymbolAddress(scratch)");
         g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return PP_OK;
@@ -146,7 +187,8 @@ extern "C" pp_status pp_fields_noalloc(int64_t N, double w, double softening, co
         e = e < -200 ? -200 : (e > 200 ? 200 : e);
         l0 = std::ldexp(1.0, e);
     }
-    NA_CUDA(launch_stage(sx, sy, sz, n, npad, stage, STAGE_F32, cx, cy, cz, 1.0 / l0, st));
+    // hi parts at stage[0, npad), lo parts at stage[npad, 2 npad)
+    NA_CUDA(launch_stage(sx, sy, sz, n, npad, stage, STAGE_F32X2, cx, cy, cz, 1.0 / l0, st));
 
     const int tiles = npad / kTile;
     const int nsplit_req = tiles < kNoAllocMaxSplit ? tiles : kNoAllocMaxSplit;
@@ -175,9 +217,9 @@ extern "C" pp_status pp_fields_noalloc(int64_t N, double w, double softening, co
     a.timeout_ns = 1000000000ull;
     void *args[] = {&a};
     const void *fn = reinterpret_cast<const void *>(
-        &force_f32_kernel<kT, kR, kTile, kStages, ACC_FP64FOLD, 4, false>);
+        &force_f32_kernel<kT, kR, kTile, kStages, ACC_FP64FOLD, 4, true>);
     NA_CUDA(cudaLaunchKernel(fn, dim3(nib * a.nsplit), dim3(kT), args,
-                             (size_t)kStages * kTile * sizeof(float4), st));
+                             (size_t)kStages * kTile * sizeof(float4) * 2, st));
     NA_CUDA(cudaMemcpyAsync(flags, err, sizeof(flags), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
     if (flags[0]) return na_fail(PP_ERR_TIMEOUT, "a device-side wait ran out of time");

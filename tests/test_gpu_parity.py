@@ -91,20 +91,29 @@ def test_fields_match_oracle(n, eps):
 # Uniform balls with 1 nm softening: the closest pairs sit ~1e3 times closer than the
 # ball radius, so single FP32 staging loses up to ~3e-5 in rel-L2 here (the FP32
 # emulation of the same arithmetic shows the same), while the a-priori bound holds.
+# The default positions mode (PP_POS_AUTO) detects this at load and stages hi/lo.
 HARD = [(777, 20e-6), (4099, 20e-6), (40000, 20e-6)]
 
 
 @pytest.mark.parametrize("acc", [capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN, capi.PP_ACC_FP64_FULL])
 @pytest.mark.parametrize("n,radius", HARD)
 def test_accumulator_modes(acc, n, radius):
+    """Each accumulation mode in the default configuration meets the field tolerance on
+    the hard balls, and every particle lies inside the a-priori bound of the staging
+    the library chose."""
     pos = wl.uniform_sphere(n, radius, seed=7 + n)
     eps = 1e-9
     ref = oracle.fields(pos, 10.0, eps)
-    E = gpu_fields(pos, 10.0, eps, acc=acc)
+    with capi.Simulation(n, 10.0, 1e-15, eps, acc=acc) as sim:
+        assert sim.get_option(capi.PP_OPT_POSITIONS_AUTO) == 1      # the default
+        sim.load(pos)
+        mode = sim.get_option(capi.PP_OPT_POSITIONS)
+        E = sim.fields()
     if acc == capi.PP_ACC_FP64_FULL:
         check_fields(E, ref, tol=1e-12, report=f"acc={acc} n={n}")
     else:
-        check_fields(E, ref, tol=1e-4, bound=bound_for(pos, 10.0, eps), report=f"acc={acc} n={n}")
+        check_fields(E, ref, bound=bound_for(pos, 10.0, eps, split=mode == capi.PP_POS_SPLIT),
+                     report=f"acc={acc} n={n} positions={mode}")
 
 
 @pytest.mark.parametrize("n,radius", HARD + [(9000, 5e-6)])
@@ -118,16 +127,32 @@ def test_split_positions_meet_tolerance_on_close_pairs(n, radius):
 
 
 def test_every_split_positions_variant():
+    """Every hi/lo-staging kernel (FP64 fold, compensated fold, per-particle weights) on
+    the hard ball; the context reports the variant that actually ran."""
     n, R = 9000, 5e-6
     pos = wl.uniform_sphere(n, R, seed=7 + n)
+    wts = 10.0 * (0.5 + wl.uniform(91, 3, n))
     ref = oracle.fields(pos, 10.0, 1e-9)
+    ref_w = oracle.fields(pos, wts, 1e-9)
     names = capi.variants()
-    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32split.", "f32x2split."))]
-    assert len(chosen) >= 4
+    chosen = [i for i, nm in enumerate(names)
+              if nm.startswith(("f32split.", "f32x2split.", "f32x2wsplit."))]
+    assert len(chosen) >= 10
     for v in chosen:
-        E = gpu_fields(pos, 10.0, 1e-9, positions=capi.PP_POS_SPLIT, variant=v)
-        check_fields(E, ref, tol=FORCE_TOL, bound=bound_for(pos, 10.0, 1e-9, split=True),
-                     report=f"split variant {names[v]}")
+        weighted = names[v].startswith("f32x2wsplit.")
+        acc = capi.PP_ACC_KAHAN if ".kahan." in names[v] else capi.PP_ACC_FP64FOLD
+        with capi.Simulation(n, 10.0, 1e-15, 1e-9, acc=acc, positions=capi.PP_POS_SPLIT) as sim:
+            sim.set_option(capi.PP_OPT_VARIANT, v)
+            if weighted:
+                sim.set_weights(wts)
+            sim.load(pos)
+            E = sim.fields()
+            assert sim.get_option(capi.PP_OPT_VARIANT) == v, names[v]
+        if weighted:
+            check_fields(E, ref_w, report=f"split variant {names[v]}")
+        else:
+            check_fields(E, ref, tol=FORCE_TOL, bound=bound_for(pos, 10.0, 1e-9, split=True),
+                         report=f"split variant {names[v]}")
 
 
 def test_auto_positions_pick_split_staging_only_when_needed():
@@ -155,6 +180,45 @@ def test_auto_positions_pick_split_staging_only_when_needed():
     err_single = rel_l2(E1, oracle.fields(pos, b.w, b.eps))
     _log("single staging gaussian65536 full", err_single, np.zeros(1), None)
     assert mode == (capi.PP_POS_SPLIT if err_single > 5e-6 else capi.PP_POS_SINGLE)
+
+
+def test_auto_staging_is_the_default_and_travels_with_the_checkpoint():
+    """PP_POS_AUTO is the default; the checkpoint frame carries the staging in force, a
+    context in AUTO adopts it (bitwise resume), one with an explicit mode keeps its own,
+    and a restore without a frame decides afresh."""
+    n, R, w, eps = 4099, 20e-6, 10.0, 1e-9
+    pos = wl.uniform_sphere(n, R, seed=7 + n)
+    dt = 0.01 / math.sqrt(2 * wl.explosion_rate(n, w, R))
+    with capi.Simulation(n, w, dt, eps) as a:
+        assert a.get_option(capi.PP_OPT_POSITIONS_AUTO) == 1
+        a.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
+        a.load(pos)
+        assert a.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        a.step(3)
+        p, v, acc, step, frame = a.state()
+        assert len(frame) == capi.PP_FRAME_LEN and frame[4] == capi.PP_POS_SPLIT
+        a.step(5)
+        ref = a.state()
+    with capi.Simulation(n, w, dt, eps) as b:
+        b.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
+        b.set_state(p, v, acc, step, frame)
+        assert b.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        b.step(5)
+        got = b.state()
+    for x, y in zip(got[:3], ref[:3]):
+        assert np.array_equal(x, y)
+    with capi.Simulation(n, w, dt, eps, positions=capi.PP_POS_SINGLE) as c:
+        c.set_state(p, v, acc, step, frame)
+        assert c.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SINGLE
+        assert c.get_option(capi.PP_OPT_POSITIONS_AUTO) == 0
+        bad = list(frame)
+        bad[4] = 2.0
+        with pytest.raises(capi.PPError) as e:
+            c.set_state(p, v, acc, step, bad)
+        assert e.value.status == capi.PP_ERR_ARG
+    with capi.Simulation(n, w, dt, eps) as d:
+        d.set_state(p, v, acc, step)
+        assert d.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
 
 
 def test_paper_lattice_fields():
@@ -188,7 +252,7 @@ def test_every_fp32_variant():
     assert len(chosen) >= 15
     for v in chosen:
         acc = capi.PP_ACC_KAHAN if ".kahan." in names[v] else capi.PP_ACC_FP64FOLD
-        with capi.Simulation(n, 2.0, 1e-15, 0.0, acc=acc) as sim:
+        with capi.Simulation(n, 2.0, 1e-15, 0.0, acc=acc, positions=capi.PP_POS_SINGLE) as sim:
             sim.set_option(capi.PP_OPT_VARIANT, v)
             sim.load(pos)
             E = sim.fields()
@@ -416,6 +480,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers(variant):
     pos = wl.gaussian_bunch(n, 2e-6, seed=41)
     with capi.Simulation(n, 1.0, 1e-15, 1e-9) as sim:
         if variant is not None:   # step with this kernel, not the resident small-N one
+            sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SINGLE)   # the kernel's staging
             sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
             sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index(variant))
         sim.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
@@ -428,8 +493,10 @@ def test_bounded_wait_reports_timeout_and_context_recovers(variant):
             sim.step(1)
         assert e.value.status == capi.PP_ERR_STATE
         sim.load(pos)
-        check_fields(sim.fields(), oracle.fields(pos, 1.0, 1e-9), tol=1e-4,
-                     bound=bound_for(pos, 1.0, 1e-9), report=f"after timeout {variant}")
+        mode = sim.get_option(capi.PP_OPT_POSITIONS)
+        check_fields(sim.fields(), oracle.fields(pos, 1.0, 1e-9),
+                     bound=bound_for(pos, 1.0, 1e-9, split=mode == capi.PP_POS_SPLIT),
+                     report=f"after timeout {variant}")
 
 
 def test_gaussian_65536_sampled_forces():

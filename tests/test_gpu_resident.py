@@ -29,9 +29,15 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
-def run(pos, vel, w, eps, dt, steps, resident, chunks=None):
+# Single FP32 staging unless a test says otherwise: most tests here are about the
+# resident kernel's single-staging forms, which PP_POS_AUTO (the default) would leave
+# for hi/lo staging on inputs with very close pairs.
+SINGLE = capi.PP_POS_SINGLE
+
+
+def run(pos, vel, w, eps, dt, steps, resident, chunks=None, positions=SINGLE):
     n = pos.shape[0]
-    with capi.Simulation(n, w, dt, eps) as sim:
+    with capi.Simulation(n, w, dt, eps, positions=positions) as sim:
         sim.set_option(capi.PP_OPT_RESIDENT, resident)
         sim.load(pos, vel)
         active = sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE)
@@ -92,11 +98,11 @@ def test_resident_is_bitwise_reproducible_across_call_grouping_and_checkpoints()
     assert one[3] == 1
     for x, y, z in zip(one[:3], again[:3], grouped[:3]):
         assert np.array_equal(x, y) and np.array_equal(x, z)
-    with capi.Simulation(n, 3.0, dt, 0.0) as sim:
+    with capi.Simulation(n, 3.0, dt, 0.0, positions=SINGLE) as sim:
         sim.load(pos)
         sim.step(11)
         state = sim.state()
-    with capi.Simulation(n, 3.0, dt, 0.0) as sim:
+    with capi.Simulation(n, 3.0, dt, 0.0, positions=SINGLE) as sim:
         sim.set_state(*state)
         sim.step(19)
         resumed = sim.state()
@@ -116,7 +122,7 @@ def test_resident_weighted_run_matches_oracle_and_per_launch(n):
     steps = 12
     out = {}
     for mode in (capi.PP_RESIDENT_AUTO, capi.PP_RESIDENT_OFF):
-        with capi.Simulation(n, 30.0, dt, eps) as sim:
+        with capi.Simulation(n, 30.0, dt, eps, positions=SINGLE) as sim:
             sim.set_option(capi.PP_OPT_RESIDENT, mode)
             sim.set_weights(w)
             sim.load(pos)
@@ -162,7 +168,7 @@ def test_resident_compensated_fold():
     dt = dt_for(n, 2.0, 2e-6)
     out = {}
     for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN):
-        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc) as sim:
+        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc, positions=SINGLE) as sim:
             sim.load(pos)
             assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
             sim.step(7)
@@ -174,7 +180,7 @@ def test_resident_compensated_fold():
     dt = dt_for(n, 2.0, 3e-6)
     acc_out = {}
     for acc in (capi.PP_ACC_FP64FOLD, capi.PP_ACC_KAHAN):
-        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc) as sim:
+        with capi.Simulation(n, 2.0, dt, 1e-9, acc=acc, positions=SINGLE) as sim:
             sim.load(pos)
             assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
             sim.step(2)
@@ -201,7 +207,7 @@ def test_resident_paper_lattice_without_softening():
 
 def test_resident_selection_rules():
     pos = wl.gaussian_bunch(3000, 2e-6, seed=73)
-    with capi.Simulation(3000, 1.0, 1e-15, 1e-9) as sim:
+    with capi.Simulation(3000, 1.0, 1e-15, 1e-9, positions=SINGLE) as sim:
         sim.load(pos)
         assert sim.get_option(capi.PP_OPT_RESIDENT) == capi.PP_RESIDENT_AUTO
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
@@ -223,16 +229,22 @@ def test_resident_selection_rules():
         sim.set_option(capi.PP_OPT_VARIANT, -1)
         sim.set_weights(np.full(3000, 1.0))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # weighted form
+        sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SPLIT)
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # weighted hi/lo: per launch
+        sim.set_weights(None)
+        sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_KAHAN)
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # compensated hi/lo: per launch
+        sim.set_option(capi.PP_OPT_ACC, capi.PP_ACC_FP64FOLD)
         with pytest.raises(capi.PPError) as e:
             sim.set_option(capi.PP_OPT_RESIDENT, 3)
         assert e.value.status == capi.PP_ERR_ARG
-    with capi.Simulation(12288, 1.0, 1e-15, 1e-9) as sim:
+    with capi.Simulation(12288, 1.0, 1e-15, 1e-9, positions=SINGLE) as sim:
         sim.load(wl.gaussian_bunch(12288, 2e-6, seed=74))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1          # the largest that fits
     with capi.Simulation(6145, 1.0, 1e-15, 1e-9, positions=capi.PP_POS_SPLIT) as sim:
         sim.load(wl.gaussian_bunch(6145, 2e-6, seed=79))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # hi/lo does not fit
-    with capi.Simulation(12289, 1.0, 1e-15, 1e-9) as sim:
+    with capi.Simulation(12289, 1.0, 1e-15, 1e-9, positions=SINGLE) as sim:
         sim.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_ON)
         sim.load(wl.gaussian_bunch(12289, 2e-6, seed=75))
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0          # does not fit
@@ -245,7 +257,7 @@ def test_resident_barrier_wait_reports_timeout_and_context_recovers(steps):
     usable again."""
     n = 3000
     pos = wl.gaussian_bunch(n, 2e-6, seed=76)
-    with capi.Simulation(n, 1.0, 1e-15, 1e-9) as sim:
+    with capi.Simulation(n, 1.0, 1e-15, 1e-9, positions=SINGLE) as sim:
         sim.set_option(capi.PP_OPT_TIMEOUT_NS, 20_000_000)
         sim.load(pos)
         assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 1
@@ -270,7 +282,7 @@ def test_autotune_keeps_small_n_steps_resident():
     n = 1500
     pos = wl.gaussian_bunch(n, 2e-6, seed=77)
     dt = dt_for(n, 2.0, 2e-6)
-    with capi.Simulation(n, 2.0, dt, 1e-9) as sim:
+    with capi.Simulation(n, 2.0, dt, 1e-9, positions=SINGLE) as sim:
         sim.load(pos)
         res = sim.autotune()
         assert res["candidates"] >= 2
