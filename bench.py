@@ -1,22 +1,22 @@
 """Benchmark: pair-interactions per second of the fused force + Velocity-Verlet step.
 
-Workload: the cold Gaussian bunch of N = 65536 macro-electrons (1e8 electrons,
-w = 1525.88), sigma = 10 um per coordinate, softening 1 nm, dt = 1e-14 s; seeded,
-synthetic.  One "step" is one time step of the whole hot path: the O(N^2) force sum
-(FP32 pairs, FP64 fold) with the push fused into its epilogue.  Throughput counts
-N^2 pair interactions per step.
+Headline workload: the cold uniform sphere of N = 2^20 macro-electrons, R = 50 um,
+Q = 1 nC (w = 5952.4), softening 5 nm, dt = 2e-14 s; seeded, synthetic.  One "step" is
+one time step of the whole hot path: the O(N^2) force sum (FP32 pairs, FP64 fold) with
+the push fused into its epilogue.  Throughput counts N^2 pair interactions per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream with a 256 MiB L2-flush write before it (outside the events).  Under
 torchrun each rank runs its own bunch (weak scaling, no data-path collective); rank 0
-prints one JSON line with the max time over ranks.  ``--impl reference`` times the
-FP64 CPU oracle instead, on bounded samples of the same workload.
+prints one JSON line with the max time over ranks.  ``--impl reference`` times the FP64
+CPU oracle instead, on bounded samples of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -37,32 +37,40 @@ from paper_2502_10640_gb300 import workloads as wl
 METRIC = "G pair-interactions/s & % FP32 peak; served p50/p99 latency at force rel-L2<=1e-5"
 UNIT = "Gpair-interactions/s"
 FLOP_PER_PAIR = 20          # counting convention for the FP32 roofline
-WORKLOAD = wl.GAUSSIAN_65536
+WORKLOAD = wl.SPHERE_1M     # the headline: the largest single-GPU configuration
+SIDE_WORKLOAD = wl.GAUSSIAN_65536
+L2_FLUSH_BYTES = 256 * 1024 * 1024
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the headline bunch (a few minutes at N = 2^20) instead of "
+                         "running the library's own plan")
     ap.add_argument("--variant", default=None,
-                    help="run this force-kernel variant (by name) instead of autotuning")
+                    help="run this force-kernel variant (by name) for the headline bunch")
     ap.add_argument("--split", type=int, default=0,
                     help="with --variant: j-split override (0 = the library's plan)")
-    ap.add_argument("--batch-steps", type=int, default=8,
+    ap.add_argument("--side-steps", type=int, default=20,
+                    help="timed steps of the N = 65536 Gaussian side figure (0 = skip)")
+    ap.add_argument("--kahan-steps", type=int, default=3,
+                    help="timed steps of the headline bunch with the compensated fold (0 = skip)")
+    ap.add_argument("--batch-steps", type=int, default=16,
                     help="steps of the 64-bunch mix, batched and one bunch per launch (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the bounded serving trace (0 = skip)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the 2^20-particle and all-FP64 comparison measurements")
+                    help="skip the all-FP64 comparison measurement")
     ap.add_argument("--lattice-steps", type=int, default=2000,
                     help="steps of the paper's 16^3 lattice, resident and per-launch (0 = skip)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -93,14 +101,28 @@ def load_peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic(variant: str, split: int):
-    """DRAM bytes per force launch of this plan (kernel variant, j-split override) from the
-    committed ncu record, or None if no capture of this plan exists or the kernel sources
-    differ from the ones the captures were taken on."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "force_f32x2_gaussian65536_traffic.json")
+def bench_config(bunch, world: int) -> dict:
+    """The `config` of the JSON line: the workload only (both arms print the same)."""
+    return {"workload": bunch.name, "N": bunch.n, "w": bunch.w, "eps_m": bunch.eps,
+            "dt_s": bunch.dt, "profile": bunch.profile, "scale_m": bunch.scale,
+            "seed": bunch.seed, "steps_of_full_run": bunch.steps,
+            "l2": "flushed before every timed step (256 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+TRAFFIC_FILES = {"sphere1m": "force_f32x2_sphere1m_traffic.json",
+                 "gaussian65536": "force_f32x2_gaussian65536_traffic.json"}
+
+
+def profiled_traffic(workload_key: str, variant: str, split: int):
+    """DRAM bytes per force launch of this plan (kernel variant, j-split override) on this
+    workload from the committed ncu record, or None if no capture of this plan exists or
+    the kernel sources differ from the ones the captures were taken on."""
+    name = TRAFFIC_FILES.get(workload_key)
+    if name is None:
+        return None
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for src in rec["sources"]:
@@ -181,36 +203,49 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def bunch_key(bunch) -> str:
+    for k, v in wl.WORKLOADS.items():
+        if v is bunch:
+            return k
+    raise KeyError(bunch.name)
+
+
+def sample_targets(n: int, m: int) -> np.ndarray:
+    """m evenly spread target indices of an n-particle bunch."""
+    return np.linspace(0, n - 1, m).astype(np.int64)
+
+
 def cpu_baseline(seconds: float, bunch=WORKLOAD):
-    """The FP64 oracle on this host's cores: fields at a bounded sample of targets
-    against all N sources (pair-interactions per second)."""
+    """The FP64 oracle on this host's cores: fields at a bounded sample of targets against
+    all N sources (pair-interactions per second), sized to about `seconds` of work."""
     import oracle
     pos = bunch.positions()
     n = bunch.n
     cores = os.cpu_count() or 1
-    m = 256
-    idx = np.arange(m, dtype=np.int64) * (n // m)
+    m = 512
     t0 = time.perf_counter()
-    oracle.fields_subset(pos, bunch.w, bunch.eps, idx)
+    oracle.fields_subset(pos, bunch.w, bunch.eps, sample_targets(n, m))
     first = time.perf_counter() - t0
     rate = m * n / max(first, 1e-9)
     m2 = int(min(n, max(m, rate * seconds / n)))
-    idx = np.linspace(0, n - 1, m2).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.fields_subset(pos, bunch.w, bunch.eps, idx)
+    oracle.fields_subset(pos, bunch.w, bunch.eps, sample_targets(n, m2))
     el = time.perf_counter() - t0
-    return {"value": m2 * n / el / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle",
+    value = m2 * n / el / 1e9
+    return {"value": value, "unit": UNIT,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
             "sample": f"FP64 oracle fields at {m2} of {n} particles against all {n} sources "
                       f"({m2 * n:.3e} pairs, {el:.1f} s)",
+            "extrapolated_s_per_step": float(n) * n / (value * 1e9),
+            "extrapolation": "one full step = N^2 pairs at the sampled rate (labelled "
+                             "extrapolation: the oracle cannot run a full step of this size "
+                             "in the bench's time)",
             "single_thread": single_thread_oracle(bunch)}
 
 
-def single_thread_oracle(bunch, targets: int = 512):
+def single_thread_oracle(bunch, targets: int = 256):
     """The same oracle call on one host thread (a child process with OMP_NUM_THREADS=1):
     `targets` sampled particles against all sources."""
-    import subprocess
-    import sys
     code = ("import sys, time, numpy as np; sys.path.insert(0, sys.argv[1]); import oracle;"
             "from paper_2502_10640_gb300 import workloads as wl;"
             f"b = wl.WORKLOADS[{bunch_key(bunch)!r}]; pos = b.positions();"
@@ -230,46 +265,92 @@ def single_thread_oracle(bunch, targets: int = 512):
                       f"({targets * bunch.n:.3e} pairs, {el:.2f} s)"}
 
 
-def bunch_key(bunch) -> str:
-    for k, v in wl.WORKLOADS.items():
-        if v is bunch:
-            return k
-    raise KeyError(bunch.name)
+def timed_steps(sim, stream, flush, steps: int):
+    """Per-step CUDA-event times (ms) of `steps` single steps on `stream`, each after an
+    L2-flush write outside the events."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        sim.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
-def run_extras(sms: int, peak_tflops: float):
-    """Side measurements on the same GPU: the single-bunch force step at N = 2^20 (the
-    size the FP32 target is stated at) and the all-FP64 path on the benchmark bunch."""
+def plan_of(sim) -> dict:
+    from paper_2502_10640_gb300 import capi
+    return {"kernel": capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)],
+            "split": sim.get_option(capi.PP_OPT_SPLIT),
+            "positions": "hi/lo" if sim.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+            else "single",
+            "positions_chosen_by": "PP_POS_AUTO" if sim.get_option(capi.PP_OPT_POSITIONS_AUTO)
+            else "explicit"}
+
+
+def roofline_record(bunch, ms_per_step: float, peak: float, plan: dict, max_mhz: float,
+                    sms: int, peak_src: str) -> dict:
+    achieved = FLOP_PER_PAIR * float(bunch.n) ** 2 / (ms_per_step / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(bunch_key(bunch), plan["kernel"], plan["split"]),
+            "note": f"{FLOP_PER_PAIR} flop per pair, N^2 pairs per launch (one launch per step); "
+                    f"peak = 2 x 128 FP32 lanes x {sms} SMs x {max_mhz:.0f} MHz "
+                    f"({'sm_max_mhz of the measured peaks file' if peak_src == 'measured' else 'fallback clock'})"}
+
+
+def run_side_figure(steps: int, stream, flush, peak: float, max_mhz: float, sms: int,
+                    peak_src: str):
+    """The N = 65536 Gaussian bunch (the second stated configuration) in the same timing
+    discipline as the headline."""
+    from paper_2502_10640_gb300 import capi
+    b = SIDE_WORKLOAD
+    with capi.Simulation(b.n, b.w, b.dt, b.eps, tune="cache") as sim:
+        sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
+        sim.load(b.positions())
+        plan = plan_of(sim)
+        sim.step(3)
+        ms = timed_steps(sim, stream, flush, steps)
+    per = sum(ms) / len(ms)
+    return {"workload": b.name, "N": b.n, "steps": steps, "ms_per_step": per,
+            "pairs_per_s": float(b.n) ** 2 / (per / 1e3), "plan": plan,
+            "roofline": roofline_record(b, per, peak, plan, max_mhz, sms, peak_src)}
+
+
+def run_kahan(steps: int, stream, flush, peak: float):
+    """The headline bunch with the compensated FP32 fold (PP_ACC_KAHAN) beside the FP64
+    fold of the headline line."""
+    from paper_2502_10640_gb300 import capi
+    b = WORKLOAD
+    with capi.Simulation(b.n, b.w, b.dt, b.eps, acc=capi.PP_ACC_KAHAN) as sim:
+        sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
+        sim.load(b.positions())
+        plan = plan_of(sim)
+        sim.step(1)
+        ms = timed_steps(sim, stream, flush, steps)
+    per = sum(ms) / len(ms)
+    pairs = float(b.n) ** 2 / (per / 1e3)
+    return {"workload": b.name, "steps": steps, "ms_per_step": per, "pairs_per_s": pairs,
+            "frac_fp32_peak": FLOP_PER_PAIR * pairs / 1e12 / peak, "plan": plan,
+            "fold": "compensated FP32 pair per component (TwoSum), converted to FP64 once"}
+
+
+def run_fp64_path():
+    """The all-FP64 comparison path on the N = 65536 bunch, one step."""
     import torch
     from paper_2502_10640_gb300 import capi
-    out = {}
-    b = wl.SPHERE_1M
-    with capi.Simulation(b.n, b.w, b.dt, b.eps, tune="cache") as sim:
-        sim.load(b.positions())
-        sim.step(1)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        stream = torch.cuda.Stream()
-        sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
-        ev[0].record(stream)
-        sim.step(3)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        sec = ev[0].elapsed_time(ev[1]) / 1e3 / 3
-        pairs = float(b.n) ** 2 / sec
-        out["sphere_2p20"] = {"workload": b.name, "pairs_per_s": pairs, "ms_per_step": sec * 1e3,
-                              "frac_fp32_peak": FLOP_PER_PAIR * pairs / 1e12 / peak_tflops,
-                              "kernel": (sim.tuned or {}).get("variant_name")}
-    g = WORKLOAD
+    g = SIDE_WORKLOAD
     with capi.Simulation(g.n, g.w, g.dt, g.eps, acc=capi.PP_ACC_FP64_FULL) as sim:
         sim.load(g.positions())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.step(1)
         sec = time.perf_counter() - t0
-        out["fp64_path"] = {"workload": g.name, "pairs_per_s": float(g.n) ** 2 / sec,
-                            "ms_per_step": sec * 1e3,
-                            "note": "FP64 pair math and accumulation, one step"}
-    return out
+    return {"workload": g.name, "pairs_per_s": float(g.n) ** 2 / sec, "ms_per_step": sec * 1e3,
+            "note": "FP64 pair math and accumulation, one step (host clock)"}
 
 
 def run_paper_lattice(steps: int):
@@ -298,64 +379,80 @@ def run_paper_lattice(steps: int):
     return out
 
 
-def run_batched(steps: int):
+def run_batched(steps: int, stream):
     """The 64-bunch mix (N log-uniform 1024-131072): one persistent launch per step for
-    all bunches, against the plain path that steps each bunch with its own launches."""
+    all bunches (autotuned kernel shape), against the plain path that steps each bunch
+    with its own launch.  Both run on one stream bracketed by CUDA events, so the plain
+    path's gaps between launches count."""
     import torch
     from paper_2502_10640_gb300 import capi
     mix = wl.batch_mix()
     pairs = float(sum(x.n ** 2 for x in mix)) * steps
-    with capi.Batch(150 << 30, graph_block=0) as bt:
-        for x in mix:
-            bt.add(x.positions(), x.w, x.dt, x.eps)
-        bt.step(1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with capi.Batch(150 << 30) as bt:
+        bt.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
+        slots = [bt.add(x.positions(), x.w, x.dt, x.eps) for x in mix]
+        n_split = sum(bt.get_option(capi.PP_OPT_POSITIONS, s) == capi.PP_POS_SPLIT for s in slots)
+        tune = bt.autotune()
+        bt.step(2)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ev[0].record(stream)
         bt.step(steps)
-        t_batch = time.perf_counter() - t0
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1e3
     sims = []
     try:
         for x in mix:
             s_ = capi.Simulation(x.n, x.w, x.dt, x.eps)
             s_.set_option(capi.PP_OPT_GRAPH_BLOCK, 0)
+            s_.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
             s_.load(x.positions())
             sims.append(s_)
         for s_ in sims:
             s_.step(1)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ev[2].record(stream)
         for _ in range(steps):
             for s_ in sims:
                 s_.step(1)
-        t_plain = time.perf_counter() - t0
+        ev[3].record(stream)
+        torch.cuda.synchronize()
     finally:
         for s_ in sims:
             s_.close()
+    t_plain = ev[2].elapsed_time(ev[3]) / 1e3
     return {"workload": f"{len(mix)} cold bunches, N log-uniform 1024-131072 (sum N^2 = "
-                        f"{pairs / steps:.3e} per step), Gaussian/sphere 50/50",
+                        f"{pairs / steps:.3e} per step), Gaussian/sphere 50/50, eps = 1e-4 R",
             "steps": steps, "unit": UNIT,
             "batched": pairs / t_batch / 1e9,
             "one_bunch_per_launch": pairs / t_plain / 1e9,
             "speedup": t_plain / t_batch,
-            "timing": "host wall clock around the synchronous step calls"}
+            "bunches_on_hi_lo_staging": int(n_split),
+            "batch_shape": tune["shape_name"],
+            "timing": "CUDA events on the shared stream around all steps of each path "
+                      "(the plain path's host gaps between its synchronous calls included)"}
 
 
 def run_serving(count: int):
-    """Bounded serving trace: Poisson arrivals at 20 requests/s of uniform-sphere runs,
-    N and step counts scaled down (x1/8 and x1/20) so the run takes seconds."""
+    """Bounded serving trace: Poisson arrivals at 20 requests/s of uniform-sphere runs
+    with N as specified (4096-524288) and step counts scaled by 1/20 so that the trace
+    finishes in about a minute."""
     from paper_2502_10640_gb300 import serve
     trace = wl.serve_trace(count)
-    reqs = serve.requests_from_trace(trace, n_scale=0.125, steps_scale=0.05)
+    reqs = serve.requests_from_trace(trace, n_scale=1.0, steps_scale=0.05)
     srv = serve.Server(150 << 30, block_steps=16)
     try:
         rep = srv.run(reqs)
     finally:
         srv.close()
-    return {"trace": f"{count} requests, Poisson 20/s, N log-uniform 512-65536 (1/8 of "
-                     f"4096-524288), steps 5-250 (1/20 of 100-5000), budget 150 GB",
+    return {"trace": f"{count} requests, Poisson 20/s, N log-uniform 4096-524288 (as "
+                     f"specified), steps 5-250 (1/20 of 100-5000), budget 150 GB",
+            "n_scale": 1.0, "steps_scale": 0.05,
             "completed": rep["completed"], "p50_latency_s": rep.get("p50_latency_s"),
             "p99_latency_s": rep.get("p99_latency_s"), "pairs_per_s": rep["pairs_per_s"],
-            "unit_pairs": "pair-interactions/s", "wall_s": rep["wall_s"], "blocks": rep["blocks"]}
+            "unit_pairs": "pair-interactions/s", "wall_s": rep["wall_s"], "blocks": rep["blocks"],
+            "mean_queueing_s": rep.get("mean_queueing_s")}
 
 
 def run_reference(args):
@@ -366,7 +463,7 @@ def run_reference(args):
     b = WORKLOAD
     pos = b.positions()
     n = b.n
-    m = 128                                            # targets per sampled step
+    m = 256                                            # targets per sampled step
     stride = n // m
     for w in range(args.warmup):
         oracle.fields_subset(pos, b.w, b.eps, np.arange(m, dtype=np.int64) * stride + w % stride)
@@ -379,16 +476,15 @@ def run_reference(args):
     pairs = args.steps * m * n
     value = pairs / t / 1e9
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"each step: FP64 oracle fields at {m} of {n} targets against all {n} sources"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded cold Gaussian bunch)",
-        "config": {"workload": b.name, "N": n, "w": b.w, "eps_m": b.eps, "dt_s": b.dt,
-                   "sample_per_step": f"fields at {m} of {n} targets against all {n} sources"},
+        "data": "synthetic (seeded cold uniform sphere)",
+        "config": bench_config(b, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: FP64 oracle fields at {m} of {n} targets "
-                                   f"against all {n} sources"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -409,48 +505,37 @@ def run_ours(args):
     capi.load()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
+    peaks, peak_src = load_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sms, max_mhz)
     b = WORKLOAD
     seed = b.seed + 1000 * rank
-    pos0 = wl.gaussian_bunch(b.n, b.scale, seed)
+    pos0 = wl.uniform_sphere(b.n, b.scale, seed)
     n = b.n
     stream = torch.cuda.Stream(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    sim = capi.Simulation(n, b.w, b.dt, b.eps)
+    sim = capi.Simulation(n, b.w, b.dt, b.eps, tune="cache" if args.autotune else None)
     sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
-    sim.load(pos0)
+    sim.load(pos0)                       # the staging decision (PP_POS_AUTO) is set-up
     if args.variant:
         sim.set_option(capi.PP_OPT_VARIANT, capi.variants().index(args.variant))
         sim.set_option(capi.PP_OPT_SPLIT, args.split)
-        tune = None
-    else:
-        tune = None if args.no_autotune else sim.autotune()     # set-up, not timed
-    plan_variant = capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)]
-    plan_split = sim.get_option(capi.PP_OPT_SPLIT)
+    plan = plan_of(sim)
+    plan["autotuned"] = bool(args.autotune)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize(dev)
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clocks:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))                     # evict L2 (outside the events)
-            starts[k].record(stream)
-            sim.step(1)
-            ends[k].record(stream)
-        torch.cuda.synchronize(dev)
+        ms = timed_steps(sim, stream, flush, args.steps)
     if world > 1:
         torch.distributed.barrier()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(ms) / 1e3
-    total_s = max_over_ranks(total_s)
-    pairs = float(n) * n * args.steps * world
-    value = pairs / total_s / 1e9
+    total_s = max_over_ranks(sum(ms) / 1e3)
+    value = float(n) * n * args.steps * world / total_s / 1e9
+    per_step_ms = 1e3 * total_s / args.steps
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -466,7 +551,7 @@ def run_ours(args):
         def e2e_run(bufs):
             nonlocal step
             t = 0.0
-            for k in range(args.e2e_steps):
+            for _ in range(args.e2e_steps):
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
                 sim.set_state(*bufs, step, frame)
@@ -481,59 +566,49 @@ def run_ours(args):
         rate = lambda t: float(n) * n * args.e2e_steps * world / t / 1e9
         e2e = {"value": rate(t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 3 * n * 3 * 8,
+               "steps": args.e2e_steps,
                "api": "pp_set_state(pinned host r,v,a) + pp_step(1) + pp_get_state(pinned host "
-                      "r,v,a), PP_MEM_HOST_MAPPED",
+                      "r,v,a), PP_MEM_HOST_MAPPED; host clock, synchronised",
                "copy_engine_value": rate(t_copy),
                "copy_engine_api": "the same calls with PP_MEM_HOST (copy engine through scratch)"}
-
     sim.close()
-    batched = run_batched(args.batch_steps) if (args.batch_steps > 0 and world == 1) else None
-    extras = None
-    if not args.no_extras and world == 1:
-        pk, _ = load_peaks()
-        extras = run_extras(sms, fp32_peak_tflops(sms, float(pk.get("sm_max_mhz", 2070.0))))
-    served = run_serving(args.serve_requests) if (args.serve_requests > 0 and world == 1) else None
-    lattice = run_paper_lattice(args.lattice_steps) if (args.lattice_steps > 0 and world == 1) else None
+
+    extras = {}
+    if world == 1:
+        if args.kahan_steps > 0:
+            extras["kahan_fold"] = run_kahan(args.kahan_steps, stream, flush, peak)
+        if args.side_steps > 0:
+            extras["gaussian_65536"] = run_side_figure(args.side_steps, stream, flush, peak,
+                                                       max_mhz, sms, peak_src)
+        if not args.no_extras:
+            extras["fp64_path"] = run_fp64_path()
+        if args.batch_steps > 0:
+            extras["batched"] = run_batched(args.batch_steps, stream)
+        if args.serve_requests > 0:
+            extras["serving"] = run_serving(args.serve_requests)
+        if args.lattice_steps > 0:
+            extras["paper_lattice"] = run_paper_lattice(args.lattice_steps)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
 
-    peaks, peak_src = load_peaks()
-    csum = clocks.summary()
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(sms, max_mhz)
-    per_step_ms = 1e3 * total_s / args.steps
-    achieved = FLOP_PER_PAIR * float(n) * n / (per_step_ms / 1e3) / 1e12
+    roof = roofline_record(b, per_step_ms, peak, plan, max_mhz, sms, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded cold Gaussian bunch)",
-        "config": {"workload": b.name, "N": n, "w": b.w, "eps_m": b.eps, "dt_s": b.dt,
-                   "precision": "FP32 pair math, FP64 per-particle fold, FP64 r/v/a",
-                   "l2": "flushed before every timed step (256 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "pct_fp32_peak": 100.0 * achieved / peak,
-                   "kernel": plan_variant,
-                   "split": plan_split,
-                   "autotuned": tune is not None},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(plan_variant, plan_split),
-                     "note": f"{FLOP_PER_PAIR} flop per pair; peak = 2 x 128 FP32 lanes x {sms} SMs x "
-                             f"{max_mhz:.0f} MHz ({'sm_max_mhz of measured peaks file' if peak_src == 'measured' else 'fallback clock'})"},
+        "data": "synthetic (seeded cold uniform sphere)",
+        "config": bench_config(b, world),
+        "precision": "FP32 pair math, FP64 per-particle fold, FP64 r/v/a",
+        "plan": plan,
+        "pct_fp32_peak": 100.0 * roof["frac"],
+        "roofline": roof,
         "gpu_launches": args.steps,
         "e2e": e2e,
-        "clocks": csum,
+        "clocks": clocks.summary(),
     }
-    if extras:
-        line.update(extras)
-    if batched:
-        line["batched"] = batched
-    if served:
-        line["serving"] = served
-    if lattice:
-        line["paper_lattice"] = lattice
+    line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -81,25 +81,38 @@ typedef enum {
 /* How staged source positions carry precision into the FP32 pair math
  * (option PP_OPT_POSITIONS).  SINGLE rounds each staged coordinate to one
  * float, so a separation d carries an absolute error of about 2^-24 |r|,
- * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs (random
- * balls of ~1e4 particles with 1 nm softening reach 3e-5 in relative L2).
+ * i.e. a relative error 2^-24 |r|/|d| that grows for close pairs: the field
+ * error of a random bunch is dominated by its few closest pairs (balls of
+ * 4e4 or 2^20 particles with nm softening exceed 1e-5 in relative L2).
  * SPLIT stages hi + lo floats (about 48 bits) and forms d = (hi_i - hi_j) +
  * (lo_i - lo_j), exact in its hi part for close pairs, at six more FP32
- * operations per pair (about 30 % slower).  SPLIT works with every FP32 pair
- * path (FP64 fold, compensated fold, per-particle weights).
+ * operations per pair (about 30 % slower).
+ * GUARDED stages hi/lo but runs the pair loop on the hi parts only, keeping
+ * per target and source tile the smallest softened squared separation s (one
+ * three-input minimum per two pairs, off the FP32 pipe); a tile holding a
+ * source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
+ * summed again for that target with hi/lo separations, and the tile holding
+ * the target block itself always is.  Pairs left to the hi parts then carry a
+ * relative error below about 5e-5 each, and the close pairs that dominate the
+ * single-staging error get split precision, at nearly single-staging speed.
+ * All three work with every FP32 pair path (FP64 fold, compensated fold,
+ * per-particle weights); the resident small-N kernel runs SINGLE and SPLIT.
  * AUTO, the default, decides whenever the library picks a staging frame
  * (pp_load_particles, pp_set_weights on a loaded context, pp_set_state
- * without a frame): it computes the fields once with each staging and keeps
- * SPLIT if the two differ by more than 5e-6 in relative L2 (the
- * single-staging error on that input, half the 1e-5 field tolerance), SINGLE
- * otherwise.  That costs two extra force passes at those calls only; steps
- * run at the speed of the staging chosen.  pp_get_option(PP_OPT_POSITIONS)
- * reports the staging in force, PP_OPT_POSITIONS_AUTO whether AUTO is on.
- * With PP_ACC_FP64_FULL sources are FP64 and the setting has no effect. */
+ * without a frame): it computes the fields with hi/lo staging and takes the
+ * first of SINGLE, SPLIT (only where the resident small-N kernel would run
+ * it), GUARDED, SPLIT whose fields differ from those by at most 5e-6 in
+ * relative L2 (half the 1e-5 field tolerance).  That costs two or three
+ * extra force passes at those calls only; steps run at the speed of the
+ * staging chosen.  pp_get_option(PP_OPT_POSITIONS) reports the staging in
+ * force, PP_OPT_POSITIONS_AUTO whether AUTO is on, pp_staging_check the
+ * measured differences.  With PP_ACC_FP64_FULL sources are FP64 and the
+ * setting has no effect. */
 typedef enum {
     PP_POS_SINGLE = 0,
     PP_POS_SPLIT = 1,
-    PP_POS_AUTO = 2       /* default */
+    PP_POS_AUTO = 2,      /* default */
+    PP_POS_GUARDED = 3
 } pp_positions;
 
 /* Option keys for pp_set_option. */
@@ -292,20 +305,39 @@ pp_status pp_check_mapped(const void *p, int64_t bytes);
 pp_status pp_fields_noalloc(int64_t N, double w, double softening, const double *pos,
                             double *E_out, void *stream);
 
+/* Outcome of pp_autotune and pp_batch_autotune. */
+typedef struct {
+    int variant;         /* chosen force-kernel variant (see pp_variant_name)       */
+    int split;           /* chosen j-split count S (j-chunks per block of targets)  */
+    double ms_per_pass;  /* measured time of one force pass with that choice, ms    */
+    int candidates;      /* number of (variant, split) pairs that were timed        */
+} pp_tune_result;
+
 /*
  * ---- Batch contexts: many independent bunches, one persistent launch per step.
  *
  * A batch holds up to 4096 bunches ("slots"), each with its own N, weight,
  * time step, softening and state, and advances all of them together: every
  * time step is one launch of a persistent kernel whose CTAs pull work items
- * (bunch, block of 512 targets, chunk of 8192 sources) from a queue.  A
- * bunch's tiling depends on its own N only, so its results are bitwise the
- * same alone or in any mix.  Device memory is admitted against the budget
- * given at creation (pp_batch_footprint says what one bunch takes).  Step
- * blocks of PP_OPT_GRAPH_BLOCK steps (even; default 16) replay a captured
- * CUDA graph.  Options: PP_OPT_STREAM, PP_OPT_GRAPH_BLOCK, PP_OPT_TIMEOUT_NS,
+ * (bunch, block of targets, chunk of 8192 sources) from a queue.  Bunches use
+ * FP32 pair math with the FP64 fold (PP_ACC_FP64FOLD) and single, hi/lo or
+ * guarded staged positions (see pp_positions), chosen per bunch when it is
+ * added: option PP_OPT_POSITIONS of the batch (default PP_POS_AUTO, which
+ * takes the first of single and guarded staging whose fields differ from the
+ * hi/lo-staged ones by at most 5e-6 for the bunch's own positions, else
+ * hi/lo; pp_batch_get_option reports a bunch's choice).  A bunch's tiling (512
+ * targets per block with single or guarded staging, 256 with hi/lo) depends on
+ * its own N and staging only, so its results are bitwise the same alone or in
+ * any mix.  Device memory is
+ * admitted against the budget given at creation (pp_batch_footprint says what
+ * one bunch takes).  Step blocks of PP_OPT_GRAPH_BLOCK steps (even; default
+ * 16) replay a captured CUDA graph.  The persistent kernel comes in several
+ * compiled shapes (threads per CTA, register budget, unrolling; see
+ * pp_batch_shape_name) that all give bitwise the same results;
+ * pp_batch_autotune times them on the current bunches.  Options:
+ * PP_OPT_STREAM, PP_OPT_GRAPH_BLOCK, PP_OPT_TIMEOUT_NS, PP_OPT_POSITIONS,
+ * PP_OPT_VARIANT (a shape index, -1 = the default shape 0),
  * PP_OPT_TEST_SKIP_COPY.
- * Bunches use single FP32 staging and the FP64 fold (PP_ACC_FP64FOLD).
  */
 typedef struct pp_batch pp_batch;
 
@@ -339,11 +371,40 @@ pp_status pp_batch_get_state(pp_batch *b, int slot, double *pos, double *vel, do
 /* Diagnostics of one bunch, as pp_diagnostics (with_pe = 0 sets pe to NaN). */
 pp_status pp_batch_diagnostics(pp_batch *b, int slot, pp_diag *out, int with_pe);
 
+/*
+ * Read an option.  slot = -1: the batch's PP_OPT_POSITIONS (for bunches added
+ * from now on), PP_OPT_VARIANT (the kernel shape), PP_OPT_GRAPH_BLOCK,
+ * PP_OPT_TIMEOUT_NS, PP_OPT_STREAM.  slot >= 0: PP_OPT_POSITIONS of that bunch
+ * (PP_POS_SINGLE, PP_POS_SPLIT or PP_POS_GUARDED: the staging it runs with).
+ * Else PP_ERR_ARG.
+ */
+pp_status pp_batch_get_option(pp_batch *b, int slot, int key, int64_t *value);
+
+/* Name of compiled batch-kernel shape `index`, or NULL past the last one. */
+const char *pp_batch_shape_name(int index);
+
+/*
+ * Batch autotuner: time one force pass (fields of the bunches' pending
+ * positions into scratch; states untouched) of every compiled shape on the
+ * active bunches and keep the fastest as PP_OPT_VARIANT.  Every shape gives
+ * bitwise the same results, so tuning never changes a result.  out->variant is
+ * the shape index, out->split 0.  PP_ERR_STATE if the batch is empty.
+ */
+pp_status pp_batch_autotune(pp_batch *b, pp_tune_result *out);
+
 /* Active bunches, device bytes in use and the budget (any pointer may be NULL). */
 pp_status pp_batch_info(pp_batch *b, int64_t *active, int64_t *bytes_used, int64_t *budget);
 
 /* Free the batch and all its bunches.  NULL is accepted. */
 pp_status pp_batch_destroy(pp_batch *b);
+
+/*
+ * The measurements of the last PP_POS_AUTO decision: relative-L2 difference
+ * of the fields with single (and, if it was tried, guarded) staging from the
+ * fields with hi/lo staging, at the positions the decision was made on; NaN
+ * where not measured.  Either pointer may be NULL.
+ */
+pp_status pp_staging_check(const pp_ctx *ctx, double *single_rel, double *guarded_rel);
 
 /* Number of particles of the context. */
 pp_status pp_get_n(const pp_ctx *ctx, int64_t *n);
@@ -363,13 +424,6 @@ const char *pp_last_error(const pp_ctx *ctx);
  */
 const char *pp_variant_name(int index);
 
-/* Outcome of pp_autotune. */
-typedef struct {
-    int variant;         /* chosen force-kernel variant (see pp_variant_name)       */
-    int split;           /* chosen j-split count S (j-chunks per block of targets)  */
-    double ms_per_pass;  /* measured time of one force pass with that choice, ms    */
-    int candidates;      /* number of (variant, split) pairs that were timed        */
-} pp_tune_result;
 
 /*
  * Autotuner: time every compiled force-kernel variant that fits the

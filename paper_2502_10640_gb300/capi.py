@@ -43,6 +43,7 @@ PP_OPT_POSITIONS_AUTO = 10
 PP_POS_SINGLE = 0
 PP_POS_SPLIT = 1
 PP_POS_AUTO = 2
+PP_POS_GUARDED = 3
 PP_FRAME_LEN = 5
 PP_OPT_TEST_SKIP_COPY = 99
 
@@ -105,6 +106,8 @@ SIGNATURES = [
     ("pp_set_state", ctypes.c_int, [_CTX, _DP, _DP, _DP, _I64, ctypes.POINTER(ctypes.c_double),
                                     ctypes.c_int]),
     ("pp_get_n", ctypes.c_int, [_CTX, ctypes.POINTER(_I64)]),
+    ("pp_staging_check", ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
     ("pp_destroy", ctypes.c_int, [_CTX]),
     ("pp_last_error", ctypes.c_char_p, [_CTX]),
     ("pp_version", ctypes.c_char_p, []),
@@ -125,6 +128,9 @@ SIGNATURES = [
     ("pp_batch_info", ctypes.c_int, [_CTX, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                      ctypes.POINTER(_I64)]),
     ("pp_batch_destroy", ctypes.c_int, [_CTX]),
+    ("pp_batch_get_option", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64)]),
+    ("pp_batch_shape_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("pp_batch_autotune", ctypes.c_int, [_CTX, ctypes.POINTER(pp_tune_result)]),
     ("pp_fields_noalloc", ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_double, _DP, _DP, _VP]),
 ]
 
@@ -238,6 +244,13 @@ def pp_get_option(ctx, key: int) -> int:
     v = _I64()
     _check(load().pp_get_option(ctx, int(key), ctypes.byref(v)), ctx)
     return v.value
+
+
+def pp_staging_check(ctx) -> dict:
+    """The last PP_POS_AUTO decision's measured field differences (NaN: not measured)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().pp_staging_check(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return {"single_rel": a.value, "guarded_rel": b.value}
 
 
 def pp_get_n(ctx) -> int:
@@ -384,17 +397,44 @@ def pp_batch_footprint(n: int) -> int:
     return b.value
 
 
+def batch_shapes() -> list[str]:
+    """Names of the compiled batch-kernel shapes (index = PP_OPT_VARIANT of a batch)."""
+    out, k = [], 0
+    while True:
+        nm = load().pp_batch_shape_name(k)
+        if nm is None:
+            return out
+        out.append(nm.decode())
+        k += 1
+
+
 class Batch:
     """Owning wrapper of a batch context (pp_batch_*): many bunches stepped together."""
 
-    def __init__(self, budget_bytes: int, graph_block: int | None = None):
+    def __init__(self, budget_bytes: int, graph_block: int | None = None,
+                 positions: int | None = None):
         self.b = _CTX()
         _check(load().pp_batch_create(int(budget_bytes), ctypes.byref(self.b)))
         if graph_block is not None:
             self.set_option(PP_OPT_GRAPH_BLOCK, graph_block)
+        if positions is not None:
+            self.set_option(PP_OPT_POSITIONS, positions)
 
     def set_option(self, key: int, value: int):
         _check(load().pp_batch_set_option(self.b, int(key), int(value)))
+
+    def get_option(self, key: int, slot: int = -1) -> int:
+        """An option of the batch (slot = -1) or of one bunch (its PP_OPT_POSITIONS)."""
+        v = _I64()
+        _check(load().pp_batch_get_option(self.b, int(slot), int(key), ctypes.byref(v)))
+        return v.value
+
+    def autotune(self) -> dict:
+        """Time every compiled shape on the current bunches; keep the fastest."""
+        r = pp_tune_result()
+        _check(load().pp_batch_autotune(self.b, ctypes.byref(r)))
+        return {"shape": r.variant, "shape_name": batch_shapes()[r.variant],
+                "ms_per_pass": r.ms_per_pass, "candidates": r.candidates}
 
     def add(self, pos, w: float, dt: float, softening: float = 0.0, vel=None) -> int:
         n = int(pos.shape[0])
@@ -518,6 +558,9 @@ class Simulation:
 
     def get_option(self, key) -> int:
         return pp_get_option(self.ctx, key)
+
+    def staging_check(self) -> dict:
+        return pp_staging_check(self.ctx)
 
     def load(self, pos, vel=None):
         pp_load_particles(self.ctx, pos, vel)

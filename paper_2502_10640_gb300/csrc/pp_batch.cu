@@ -35,35 +35,55 @@ pp_status bcuda(cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return bcuda(e_, #call);    \
     } while (0)
 
+// Tiling of one bunch: a function of its N and of its staging only.
 struct Layout {
     int npad, nib, nipad, nsplit, jchunk;
-    size_t state_bytes, stage_bytes, partial_bytes, ticket_bytes, total;
 };
 
-// Device bytes of one bunch; a function of N only.
-Layout layout_for(int64_t n)
+Layout layout_for(int64_t n, int staging)
 {
     Layout L{};
+    const int bi = batch_block(staging);
     L.npad = (int)((n + kPad - 1) / kPad * kPad);
-    L.nib = (int)((n + kBatchBI - 1) / kBatchBI);
-    L.nipad = L.nib * kBatchBI;
+    L.nib = (int)((n + bi - 1) / bi);
+    L.nipad = L.nib * bi;
     L.jchunk = kBatchJChunk;
     L.nsplit = (L.npad + L.jchunk - 1) / L.jchunk;
-    L.state_bytes = (size_t)9 * L.npad * sizeof(double);
-    L.stage_bytes = (size_t)L.npad * sizeof(float4);
-    L.partial_bytes = L.nsplit > 1 ? (size_t)L.nsplit * 3 * L.nipad * sizeof(double) : 0;
-    L.ticket_bytes = (size_t)L.nib * sizeof(unsigned);
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    L.total = al(L.state_bytes) + 2 * al(L.stage_bytes) + al(L.partial_bytes) +
-              al(L.ticket_bytes) + al((size_t)3 * n * sizeof(double));
     return L;
+}
+
+// Device memory of one bunch, laid out to hold either staging (so the footprint
+// is a function of N only): state, two staging buffers of 32 bytes per source
+// (hi/lo), partial sums and tickets for the larger of the two tilings, and an
+// [N][3] transfer buffer.
+struct Footprint {
+    size_t state_bytes, stage_bytes, partial_bytes, ticket_bytes, aos_bytes, total;
+};
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+Footprint footprint_for(int64_t n)
+{
+    const Layout a = layout_for(n, POS_SINGLE), b = layout_for(n, POS_SPLIT);
+    Footprint F{};
+    F.state_bytes = (size_t)9 * a.npad * sizeof(double);
+    F.stage_bytes = (size_t)2 * a.npad * sizeof(float4);
+    const size_t nipad = (size_t)std::max(a.nipad, b.nipad);
+    F.partial_bytes = a.nsplit > 1 ? (size_t)a.nsplit * 3 * nipad * sizeof(double) : 0;
+    F.ticket_bytes = (size_t)std::max(a.nib, b.nib) * sizeof(unsigned);
+    F.aos_bytes = (size_t)3 * n * sizeof(double);
+    F.total = al256(F.state_bytes) + 2 * al256(F.stage_bytes) + al256(F.partial_bytes) +
+              al256(F.ticket_bytes) + al256(F.aos_bytes);
+    return F;
 }
 
 struct Slot {
     bool active = false;
     int64_t n = 0;
     double w = 1, dt = 0, eps = 0;
+    int staging = POS_SINGLE;      // POS_SINGLE, POS_SPLIT or POS_GUARDED (set at pp_batch_add)
     Layout L{};
+    Footprint F{};
     unsigned char *mem = nullptr;  // one allocation holding everything below
     double *r[3] = {}, *v[3] = {}, *a[3] = {};
     void *stage[2] = {};
@@ -75,18 +95,52 @@ struct Slot {
     double cx = 0, cy = 0, cz = 0, l0 = 1;
 };
 
+// Compiled shapes of the batch kernel (see pp_batch.cuh: all give bitwise the
+// same results).  The first is the default.
+struct Shape {
+    const char *name;
+    const void *fn;
+    int threads;
+};
+
+template <int T, int MINB, int UNROLL>
+Shape make_shape(const char *name)
+{
+    return Shape{name,
+                 reinterpret_cast<const void *>(
+                     &batch_f32x2_kernel<T, kBatchTile, kBatchStages, MINB, UNROLL>),
+                 T};
+}
+
+const Shape kShapes[] = {
+    make_shape<128, 4, 2>("t128m4u2"),
+    make_shape<128, 4, 1>("t128m4u1"),
+    make_shape<128, 3, 2>("t128m3u2"),
+    make_shape<256, 2, 1>("t256m2u1"),
+    make_shape<256, 2, 2>("t256m2u2"),
+};
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+
+size_t batch_smem()
+{
+    return (size_t)kBatchStages * kBatchTile * sizeof(float4) +
+           (size_t)3 * kBatchBIMax * sizeof(double);
+}
+
 }  // namespace
 
 struct pp_batch {
     int device = 0;
     int sms = 0;
-    int grid = 0;
+    int shape = 0;                    // index into kShapes
+    int grid = 0;                     // persistent CTAs of that shape
+    int positions = PP_POS_AUTO;      // staging of bunches added from now on
     cudaStream_t own_stream = nullptr, stream = nullptr;
     int64_t budget = 0, used = 0;
     std::vector<Slot> slots;
     BunchDesc *d_descs = nullptr;     // [kMaxBunches]
     BatchHeader *d_hdr = nullptr;
-    BunchDesc *d_init_desc = nullptr; // one bunch, for the initial force pass
+    BunchDesc *d_init_desc = nullptr; // one bunch, for its own passes at pp_batch_add
     BatchHeader *d_init_hdr = nullptr;
     unsigned *d_queue = nullptr;
     int *d_err = nullptr;             // [0] wait ran out, [1] non-finite input
@@ -103,17 +157,6 @@ struct pp_batch {
 
 namespace {
 
-const void *batch_kernel()
-{
-    return reinterpret_cast<const void *>(
-        &batch_f32x2_kernel<kBatchT, kBatchR, kBatchTile, kBatchStages, kBatchMinB>);
-}
-
-size_t batch_smem()
-{
-    return (size_t)kBatchStages * kBatchTile * sizeof(float4) + (size_t)3 * kBatchBI * sizeof(double);
-}
-
 void drop_graph(pp_batch *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -121,7 +164,23 @@ void drop_graph(pp_batch *b)
     b->graph_steps = 0;
 }
 
-BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base)
+// Make shape k the batch's kernel: shared-memory attribute and persistent grid
+// (one CTA per resident slot on every SM).
+pp_status select_shape(pp_batch *b, int k)
+{
+    const Shape &sh = kShapes[k];
+    B_CUDA(cudaFuncSetAttribute(sh.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_smem()));
+    int occ = 0;
+    B_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sh.fn, sh.threads, batch_smem()));
+    if (occ < 1) return bfail(PP_ERR_CUDA, "batch kernel does not fit on an SM");
+    b->shape = k;
+    b->grid = b->sms * occ;
+    drop_graph(b);
+    return PP_OK;
+}
+
+BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base, double *out = nullptr)
 {
     BunchDesc d{};
     d.stage[0] = s.stage[0];
@@ -133,6 +192,7 @@ BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base)
     }
     d.partial = s.partial;
     d.tickets = s.tickets;
+    d.out = out;
     d.n = (int)s.n;
     d.npad = s.L.npad;
     d.nib = s.L.nib;
@@ -142,9 +202,12 @@ BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base)
     d.item_base = item_base;
     d.parity0 = parity0;
     d.mode = mode;
+    d.staging = s.staging;
     const double epsl = s.eps / s.l0;
     d.eps2f = (float)(epsl * epsl);
+    // a = k e^2 w / (m_e L0^2) * sum (Eq. F with Eq. E); E = (m_e / q_e) a, q_e = -e
     d.cscale = kCoulomb * kE * kE * s.w / (kMe * s.l0 * s.l0);
+    d.escale = -kCoulomb * kE * s.w / (s.l0 * s.l0);
     d.dt = s.dt;
     d.half_dt = s.dt / 2.0;
     d.half_dt2 = s.dt * s.dt / 2.0;
@@ -155,10 +218,12 @@ BunchDesc make_desc(const Slot &s, int mode, int parity0, int item_base)
     return d;
 }
 
+int stage_kind_of(const Slot &s) { return s.staging == POS_SINGLE ? STAGE_F32I : STAGE_F32IX2; }
+
 pp_status launch_batch(pp_batch *b, const BunchDesc *descs, const BatchHeader *hdr, int step_k)
 {
     B_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
-    const void *fn = batch_kernel();
+    const Shape &sh = kShapes[b->shape];
     int *err = b->d_err;
     unsigned *queue = b->d_queue;
     unsigned long long tmo = b->timeout_ns;
@@ -166,7 +231,7 @@ pp_status launch_batch(pp_batch *b, const BunchDesc *descs, const BatchHeader *h
     b->skip_copy = 0;
     void *args[] = {(void *)&descs, (void *)&hdr, (void *)&queue, (void *)&step_k, (void *)&err,
                     (void *)&tmo, (void *)&skip};
-    B_CUDA(cudaLaunchKernel(fn, dim3(b->grid), dim3(kBatchT), args, batch_smem(), b->stream));
+    B_CUDA(cudaLaunchKernel(sh.fn, dim3(b->grid), dim3(sh.threads), args, batch_smem(), b->stream));
     return PP_OK;
 }
 
@@ -181,12 +246,13 @@ pp_status read_errors(pp_batch *b, int *flags)
     return PP_OK;
 }
 
-// Rewrite the device table of active bunches.  Table order: largest source
-// chunk first (ties by slot), so that the queue hands out the full-size items
-// of the big bunches first and the short items of small bunches fill the tail
-// of the step (longest-processing-time-first).  The order changes only which
-// CTA takes an item, never an item's arithmetic.
-pp_status upload_table(pp_batch *b)
+// Device table of the active bunches in `mode` (MODE_STEP for stepping; MODE_FIELDS
+// writes each bunch's field into its transfer buffer).  Table order: largest source
+// chunk first (ties by slot), so that the queue hands out the full-size items of the
+// big bunches first and the short items of small bunches fill the tail of the step
+// (longest-processing-time-first).  The order changes only which CTA takes an
+// item, never an item's arithmetic.
+pp_status write_table(pp_batch *b, int mode)
 {
     std::vector<BunchDesc> h;
     b->order.clear();
@@ -199,7 +265,7 @@ pp_status upload_table(pp_batch *b)
     int items = 0;
     for (int i : b->order) {
         const Slot &s = b->slots[i];
-        h.push_back(make_desc(s, MODE_STEP, s.parity, items));
+        h.push_back(make_desc(s, mode, s.parity, items, mode == MODE_FIELDS ? s.aos : nullptr));
         items += s.L.nib * s.L.nsplit;
     }
     BatchHeader hdr{(int)h.size(), items};
@@ -208,9 +274,11 @@ pp_status upload_table(pp_batch *b)
                                cudaMemcpyHostToDevice, b->stream));
     B_CUDA(cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, b->stream));
     B_CUDA(cudaStreamSynchronize(b->stream));
-    b->dirty = false;
+    b->dirty = mode != MODE_STEP;
     return PP_OK;
 }
+
+pp_status upload_table(pp_batch *b) { return write_table(b, MODE_STEP); }
 
 pp_status slot_moments(pp_batch *b, Slot &s, int pass, double cx, double cy, double cz,
                        double out[kMomSlots])
@@ -221,6 +289,73 @@ pp_status slot_moments(pp_batch *b, Slot &s, int pass, double cx, double cy, dou
                            cudaMemcpyDeviceToHost, b->stream));
     B_CUDA(cudaStreamSynchronize(b->stream));
     std::memcpy(out, b->mom_host, kMomSlots * sizeof(double));
+    return PP_OK;
+}
+
+// One pass of the batch kernel over a single bunch (its own tiling), from
+// positions staged into stage[1]: MODE_INIT (a_0, stages r_1 into stage[0]) or
+// MODE_FIELDS (E into `out`).
+pp_status slot_pass(pp_batch *b, Slot &s, int mode, double *out)
+{
+    BunchDesc d = make_desc(s, mode, 1, 0, out);
+    BatchHeader h{1, s.L.nib * s.L.nsplit};
+    B_CUDA(cudaMemcpyAsync(b->d_init_desc, &d, sizeof(d), cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(cudaMemcpyAsync(b->d_init_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream));
+    return launch_batch(b, b->d_init_desc, b->d_init_hdr, 0);
+}
+
+// Field of one bunch at its current positions with staging `staging` (the batch
+// kernel, the bunch's own tiling for that staging), from sources staged into
+// stage[1], into out.
+pp_status slot_fields(pp_batch *b, Slot &s, int staging, double *out)
+{
+    s.staging = staging;
+    s.L = layout_for(s.n, staging);
+    B_CUDA(launch_stage(s.r[0], s.r[1], s.r[2], (int)s.n, s.L.npad, s.stage[1], stage_kind_of(s),
+                        s.cx, s.cy, s.cz, 1.0 / s.l0, b->stream));
+    return slot_pass(b, s, MODE_FIELDS, out);
+}
+
+// |a - b| / |b| (relative L2) of two device [n][3] arrays; synchronises.
+pp_status slot_rel_diff(pp_batch *b, const Slot &s, const double *a, const double *ref,
+                        double *rel)
+{
+    B_CUDA(launch_diff_norms(a, ref, (int)(3 * s.n), b->mom_partials, b->stream));
+    double h[2 * kDiffBlocks];
+    B_CUDA(cudaMemcpyAsync(h, b->mom_partials, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    int flags[2] = {0, 0};
+    if (pp_status st = read_errors(b, flags)) return st;
+    if (flags[0]) return bfail(PP_ERR_TIMEOUT, "a device-side wait ran out of time");
+    double d2 = 0.0, b2 = 0.0;
+    for (int k = 0; k < kDiffBlocks; ++k) {
+        d2 += h[2 * k];
+        b2 += h[2 * k + 1];
+    }
+    *rel = b2 > 0 ? std::sqrt(d2 / b2) : 0.0;
+    return PP_OK;
+}
+
+// PP_POS_AUTO for one bunch: the first of single and guarded staging whose field
+// differs from the hi/lo-staged one by at most 5e-6 in relative L2 (half the 1e-5
+// field tolerance), else hi/lo staging.  The decision reads nothing but the bunch's
+// own positions, so it is the same alone and in any mix.
+pp_status decide_slot_staging(pp_batch *b, Slot &s, int *staging)
+{
+    // the hi/lo field goes to stage[0] (32 bytes per source: room for [N][3]
+    // doubles), a candidate's to the transfer buffer; sources in stage[1]
+    double *e_split = static_cast<double *>(s.stage[0]);
+    double *e_cand = s.aos;
+    double rel = 0.0;
+    if (pp_status st = slot_fields(b, s, POS_SPLIT, e_split)) return st;
+    for (int cand : {POS_SINGLE, POS_GUARDED}) {
+        if (pp_status st = slot_fields(b, s, cand, e_cand)) return st;
+        if (pp_status st = slot_rel_diff(b, s, e_cand, e_split, &rel)) return st;
+        if (rel <= 5e-6) {
+            *staging = cand;
+            return PP_OK;
+        }
+    }
+    *staging = POS_SPLIT;
     return PP_OK;
 }
 
@@ -306,7 +441,7 @@ pp_status check_slot(const pp_batch *b, int slot)
 void free_slot(pp_batch *b, Slot &s)
 {
     if (s.mem) cudaFree(s.mem);
-    b->used -= (int64_t)s.L.total;
+    b->used -= (int64_t)s.F.total;
     s = Slot{};
 }
 
@@ -317,7 +452,7 @@ extern "C" {
 pp_status pp_batch_footprint(int64_t N, int64_t *bytes)
 {
     if (!bytes || N < 1 || N > (int64_t(1) << 28)) return bfail(PP_ERR_ARG, "bad N or null bytes");
-    *bytes = (int64_t)layout_for(N).total;
+    *bytes = (int64_t)footprint_for(N).total;
     return PP_OK;
 }
 
@@ -358,14 +493,10 @@ pp_status pp_batch_create(int64_t budget_bytes, pp_batch **out)
     if (cudaGetDevice(&b->device) != cudaSuccess) return bail(PP_ERR_CUDA, "no CUDA device");
     if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
         return bail(PP_ERR_CUDA, "cannot query SM count");
-    if (cudaFuncSetAttribute(batch_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batch_smem()) != cudaSuccess)
+    if (select_shape(b, 0) != PP_OK) {
+        cudaGetLastError();
         return bail(PP_ERR_CUDA, "cannot configure the batch kernel");
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(), kBatchT, batch_smem()) !=
-            cudaSuccess || occ < 1)
-        return bail(PP_ERR_CUDA, "batch kernel does not fit on an SM");
-    b->grid = b->sms * occ;
+    }
     if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PP_ERR_CUDA, "cudaStreamCreate failed");
     b->stream = b->own_stream;
@@ -416,9 +547,102 @@ pp_status pp_batch_set_option(pp_batch *b, int key, int64_t value)
         drop_graph(b);
         b->timeout_ns = (uint64_t)value;
         return PP_OK;
+    case PP_OPT_POSITIONS:
+        if (value != PP_POS_SINGLE && value != PP_POS_SPLIT && value != PP_POS_AUTO &&
+            value != PP_POS_GUARDED)
+            return bfail(PP_ERR_ARG, "bad positions mode");
+        b->positions = (int)value;
+        return PP_OK;
+    case PP_OPT_VARIANT:
+        if (value < -1 || value >= kNumShapes) return bfail(PP_ERR_ARG, "no such batch shape");
+        B_CUDA(cudaSetDevice(b->device));
+        return select_shape(b, value < 0 ? 0 : (int)value);
     default:
         return bfail(PP_ERR_ARG, "option not supported by batch contexts");
     }
+}
+
+pp_status pp_batch_get_option(pp_batch *b, int slot, int key, int64_t *value)
+{
+    if (!b || !value) return bfail(PP_ERR_ARG, "null argument");
+    if (slot >= 0) {
+        if (pp_status st = check_slot(b, slot)) return st;
+        if (key != PP_OPT_POSITIONS) return bfail(PP_ERR_ARG, "option not kept per bunch");
+        *value = b->slots[slot].staging;
+        return PP_OK;
+    }
+    if (slot != -1) return bfail(PP_ERR_ARG, "slot must be -1 (the batch) or a bunch's slot");
+    switch (key) {
+    case PP_OPT_POSITIONS: *value = b->positions; return PP_OK;
+    case PP_OPT_VARIANT: *value = b->shape; return PP_OK;
+    case PP_OPT_GRAPH_BLOCK: *value = b->graph_block; return PP_OK;
+    case PP_OPT_TIMEOUT_NS: *value = (int64_t)b->timeout_ns; return PP_OK;
+    case PP_OPT_STREAM: *value = (int64_t)reinterpret_cast<intptr_t>(b->stream); return PP_OK;
+    default: return bfail(PP_ERR_ARG, "unknown option key");
+    }
+}
+
+const char *pp_batch_shape_name(int index)
+{
+    return (index >= 0 && index < kNumShapes) ? kShapes[index].name : nullptr;
+}
+
+pp_status pp_batch_autotune(pp_batch *b, pp_tune_result *out)
+{
+    NvtxRange nvtx_("pp_batch_autotune");
+    if (!b) return bfail(PP_ERR_ARG, "null batch");
+    B_CUDA(cudaSetDevice(b->device));
+    int nactive = 0;
+    for (auto &s : b->slots) nactive += s.active;
+    if (nactive == 0) return bfail(PP_ERR_STATE, "no bunches to tune on");
+    // MODE_FIELDS passes over every active bunch (fields into the transfer buffers):
+    // the bunches' states are untouched
+    if (pp_status st = write_table(b, MODE_FIELDS)) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    B_CUDA(cudaEventCreate(&e0));
+    B_CUDA(cudaEventCreate(&e1));
+    const int saved = b->shape;
+    int best = -1;
+    double best_ms = 1e300;
+    pp_status st = PP_OK;
+    for (int k = 0; k < kNumShapes && st == PP_OK; ++k) {
+        st = select_shape(b, k);
+        if (st != PP_OK) break;
+        st = launch_batch(b, b->d_descs, b->d_hdr, 0);   // untimed first pass
+        if (st != PP_OK) break;
+        constexpr int kReps = 3;
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < kReps && st == PP_OK; ++r) st = launch_batch(b, b->d_descs, b->d_hdr, 0);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = bcuda(cudaGetLastError(), "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / kReps < best_ms) {
+            best_ms = ms / kReps;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int flags[2] = {0, 0};
+    if (st == PP_OK) st = read_errors(b, flags);
+    if (st == PP_OK && flags[0]) st = bfail(PP_ERR_TIMEOUT, "a device-side wait ran out of time");
+    b->dirty = true;   // the step table is rewritten before the next step
+    if (st != PP_OK || best < 0) {
+        select_shape(b, saved);
+        return st != PP_OK ? st : bfail(PP_ERR_STATE, "no shape could be timed");
+    }
+    if (pp_status s2 = select_shape(b, best)) return s2;
+    if (out) {
+        out->variant = best;
+        out->split = 0;
+        out->ms_per_pass = best_ms;
+        out->candidates = kNumShapes;
+    }
+    return PP_OK;
 }
 
 pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softening,
@@ -433,8 +657,8 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
         !(std::isfinite(softening) && softening >= 0))
         return bfail(PP_ERR_ARG, "w, dt must be finite and > 0; softening finite and >= 0");
     B_CUDA(cudaSetDevice(b->device));
-    const Layout L = layout_for(N);
-    if (b->used + (int64_t)L.total > b->budget)
+    const Footprint F = footprint_for(N);
+    if (b->used + (int64_t)F.total > b->budget)
         return bfail(PP_ERR_NOMEM, "the bunch does not fit in the remaining memory budget");
     int idx = -1;
     for (int i = 0; i < (int)b->slots.size(); ++i)
@@ -455,30 +679,31 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
     s.w = w;
     s.dt = dt;
     s.eps = softening;
-    s.L = L;
-    if (cudaMalloc(&s.mem, L.total) != cudaSuccess) {
+    s.F = F;
+    s.staging = b->positions == PP_POS_AUTO ? POS_SINGLE : b->positions;
+    s.L = layout_for(N, s.staging);
+    if (cudaMalloc(&s.mem, F.total) != cudaSuccess) {
         cudaGetLastError();
         s = Slot{};
         return bfail(PP_ERR_NOMEM, "device allocation failed");
     }
-    b->used += (int64_t)L.total;
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    b->used += (int64_t)F.total;
     unsigned char *p = s.mem;
     double *state = reinterpret_cast<double *>(p);
-    p += al(L.state_bytes);
+    p += al256(F.state_bytes);
     for (int c = 0; c < 3; ++c) {
-        s.r[c] = state + (size_t)(0 + c) * L.npad;
-        s.v[c] = state + (size_t)(3 + c) * L.npad;
-        s.a[c] = state + (size_t)(6 + c) * L.npad;
+        s.r[c] = state + (size_t)(0 + c) * s.L.npad;
+        s.v[c] = state + (size_t)(3 + c) * s.L.npad;
+        s.a[c] = state + (size_t)(6 + c) * s.L.npad;
     }
     s.stage[0] = p;
-    p += al(L.stage_bytes);
+    p += al256(F.stage_bytes);
     s.stage[1] = p;
-    p += al(L.stage_bytes);
+    p += al256(F.stage_bytes);
     s.partial = reinterpret_cast<double *>(p);
-    p += al(L.partial_bytes);
+    p += al256(F.partial_bytes);
     s.tickets = reinterpret_cast<unsigned *>(p);
-    p += al(L.ticket_bytes);
+    p += al256(F.ticket_bytes);
     s.aos = reinterpret_cast<double *>(p);
     s.active = true;
     auto undo = [&](pp_status st, const std::string &m) {
@@ -486,8 +711,8 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
         return bfail(st, m);
     };
     const size_t bytes = (size_t)N * 3 * sizeof(double);
-    if (cudaMemsetAsync(state, 0, L.state_bytes, b->stream) != cudaSuccess ||
-        cudaMemsetAsync(s.tickets, 0, L.ticket_bytes, b->stream) != cudaSuccess)
+    if (cudaMemsetAsync(state, 0, F.state_bytes, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(s.tickets, 0, F.ticket_bytes, b->stream) != cudaSuccess)
         return undo(PP_ERR_CUDA, "memset failed");
     const double *src = pos;
     if (on_device != PP_MEM_DEVICE) {
@@ -520,17 +745,21 @@ pp_status pp_batch_add(pp_batch *b, int64_t N, double w, double dt, double softe
     const double rms = std::sqrt(m[0] / N);
     s.l0 = 1.0;
     if (std::isfinite(rms) && rms > 0) s.l0 = std::ldexp(1.0, std::max(-200, std::min(200, (int)std::lround(std::log2(rms)))));
-    // a_0 = F(r_0) with the batch kernel itself (identical tiling), staging r_1
-    if (launch_fill_padding(s.stage[0], (int)N, L.npad, STAGE_F32I, b->stream) != cudaSuccess ||
-        launch_stage(s.r[0], s.r[1], s.r[2], (int)N, L.npad, s.stage[1], STAGE_F32I, s.cx, s.cy,
-                     s.cz, 1.0 / s.l0, b->stream) != cudaSuccess)
+    if (b->positions == PP_POS_AUTO) {
+        int staging = POS_SPLIT;
+        if (pp_status st = decide_slot_staging(b, s, &staging)) {
+            const std::string msg = pp_last_error(nullptr);
+            return undo(st, msg);
+        }
+        s.staging = staging;
+        s.L = layout_for(N, s.staging);
+    }
+    // a_0 = F(r_0) with the batch kernel itself (the bunch's own tiling), staging r_1
+    if (launch_fill_padding(s.stage[0], (int)N, s.L.npad, stage_kind_of(s), b->stream) != cudaSuccess ||
+        launch_stage(s.r[0], s.r[1], s.r[2], (int)N, s.L.npad, s.stage[1], stage_kind_of(s), s.cx,
+                     s.cy, s.cz, 1.0 / s.l0, b->stream) != cudaSuccess)
         return undo(PP_ERR_CUDA, "staging failed");
-    BunchDesc d = make_desc(s, MODE_INIT, 1, 0);
-    BatchHeader h{1, L.nib * L.nsplit};
-    if (cudaMemcpyAsync(b->d_init_desc, &d, sizeof(d), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_init_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
-        return undo(PP_ERR_CUDA, "table upload failed");
-    if (launch_batch(b, b->d_init_desc, b->d_init_hdr, 0) != PP_OK)
+    if (slot_pass(b, s, MODE_INIT, nullptr) != PP_OK)
         return undo(PP_ERR_CUDA, "initial force pass failed to launch");
     if (read_errors(b, flags) != PP_OK) return undo(PP_ERR_CUDA, "error word read failed");
     if (flags[0]) return undo(PP_ERR_TIMEOUT, "a device-side wait ran out of time");

@@ -81,9 +81,10 @@ struct pp_ctx {
     double cx = 0, cy = 0, cz = 0, l0 = 1;
 
     int acc = PP_ACC_FP64FOLD;
-    int positions = PP_POS_SINGLE;   // in force: SINGLE or SPLIT
+    int positions = PP_POS_SINGLE;   // in force: SINGLE, SPLIT or GUARDED
     bool positions_auto = true;      // PP_POS_AUTO (the default): decide at every load
-    double auto_rel = -1.0;          // last AUTO estimate of the single-staging error
+    double auto_rel_single = NAN;    // last AUTO measurements against hi/lo staging
+    double auto_rel_guarded = NAN;
     int split_override = 0;
     int variant_override = -1;
     int graph_block = 16;
@@ -132,9 +133,21 @@ const Variant *force_variant(const pp_ctx *c)
     const int want_kind = c->wts ? KIND_FORCE32W : KIND_FORCE32;
     if (c->variant_override >= 0 && c->variant_override < count) {
         const Variant &v = vs[c->variant_override];
-        const bool split = v.stage == STAGE_F32X2 || v.stage == STAGE_F32IX2;
-        if (v.kind == want_kind && v.acc == c->acc && split == (c->positions == PP_POS_SPLIT))
-            return &v;
+        if (v.kind == want_kind && v.acc == c->acc && v.positions == c->positions) return &v;
+    }
+    const bool big = c->n >= 32768, mid = c->n >= 8192;
+    if (c->positions == PP_POS_GUARDED) {   // hi/lo staged, hi parts streamed
+        if (c->wts)
+            return variant_by_name(big ? "f32x2wguard.sfold64.t128r4k512m4"
+                                       : mid ? "f32x2wguard.fold64.t128r2k128"
+                                             : "f32x2wguard.fold64.t64r1k128");
+        if (c->acc == PP_ACC_KAHAN)
+            return variant_by_name(big ? "f32x2guard.kahan.st128r4k512m4u1"
+                                       : mid ? "f32x2guard.kahan.t128r2k128"
+                                             : "f32x2guard.kahan.t64r1k128");
+        return variant_by_name(big ? "f32x2guard.sfold64.t128r4k1024s2m4u1"
+                                   : mid ? "f32x2guard.fold64.t128r2k128"
+                                         : "f32x2guard.fold64.t64r1k128");
     }
     if (c->wts && c->positions == PP_POS_SPLIT) {  // weights on hi/lo staged sources
         if (c->n >= 32768) return variant_by_name("f32x2wsplit.sfold64.t128r2k512m4");
@@ -614,91 +627,6 @@ pp_status check_ctx(const pp_ctx *c)
 }
 
 
-// Deterministic sums of |a - b|^2 and |b|^2 over n [3]-vectors (one pass per
-// block, fixed tree, then the host adds the block results in order).
-constexpr int kDiffBlocks = 120, kDiffThreads = 256;
-
-__global__ void __launch_bounds__(kDiffThreads)
-    diff_norms_kernel(const double *__restrict__ a, const double *__restrict__ b, int n3,
-                      double *partials)
-{
-    __shared__ double sd[kDiffThreads], sb[kDiffThreads];
-    const int chunk = (n3 + gridDim.x - 1) / gridDim.x;
-    const int lo = blockIdx.x * chunk, hi = min(n3, lo + chunk);
-    double d2 = 0.0, b2 = 0.0;
-    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-        const double d = a[k] - b[k];
-        d2 += d * d;
-        b2 += b[k] * b[k];
-    }
-    sd[threadIdx.x] = d2;
-    sb[threadIdx.x] = b2;
-    __syncthreads();
-    for (int s = kDiffThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sd[threadIdx.x] += sd[threadIdx.x + s];
-            sb[threadIdx.x] += sb[threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = sd[0];
-        partials[2 * blockIdx.x + 1] = sb[0];
-    }
-}
-
-// PP_POS_AUTO: fields of the current positions with single and with split
-// staging; keep split staging if they differ by more than 5e-6 (relative L2),
-// half the 1e-5 tolerance, so single staging is kept only with a 2x margin.
-pp_status decide_positions(pp_ctx *c)
-{
-    if (f64_pairs(c)) return PP_OK;   // FP64 sources: nothing to choose
-    const size_t bytes = (size_t)c->n * 3 * sizeof(double);
-    double *e_split = nullptr, *parts = nullptr;
-    if (cudaMalloc(&e_split, bytes) != cudaSuccess ||
-        cudaMalloc(&parts, 2 * kDiffBlocks * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(e_split);
-        return fail(PP_ERR_NOMEM, "cannot allocate the positions-mode check");
-    }
-    void *scratch = c->stage[c->parity ^ 1];
-    pp_status st = PP_OK;
-    double h[2 * kDiffBlocks];
-    c->positions = PP_POS_SINGLE;
-    st = stage_current(c, scratch, stage_kind(c));
-    if (st == PP_OK) st = force_pass(c, MODE_FIELDS, scratch, nullptr, c->aos);
-    if (st == PP_OK) {
-        c->positions = PP_POS_SPLIT;
-        st = stage_current(c, scratch, stage_kind(c));
-    }
-    if (st == PP_OK) st = force_pass(c, MODE_FIELDS, scratch, nullptr, e_split);
-    if (st == PP_OK) {
-        diff_norms_kernel<<<kDiffBlocks, kDiffThreads, 0, c->stream>>>(c->aos, e_split,
-                                                                     (int)(3 * c->n), parts);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h, parts, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "positions-mode check");
-    }
-    cudaFree(e_split);
-    cudaFree(parts);
-    if (st == PP_OK) st = check_device_errors(c, true);
-    if (st != PP_OK) {
-        c->positions = PP_POS_SINGLE;
-        return st;
-    }
-    double d2 = 0.0, b2 = 0.0;
-    for (int k = 0; k < kDiffBlocks; ++k) {
-        d2 += h[2 * k];
-        b2 += h[2 * k + 1];
-    }
-    c->auto_rel = b2 > 0 ? std::sqrt(d2 / b2) : 0.0;
-    c->positions = c->auto_rel > 5e-6 ? PP_POS_SPLIT : PP_POS_SINGLE;
-    drop_graphs(c);
-    return PP_OK;
-}
-
 // ---- resident small-N stepping ------------------------------------------------
 // Largest N whose staged sources fit one CTA's shared memory alongside the
 // partial sums (npad = 12288: 192 KB + 12 KB); hi/lo staging needs twice the
@@ -724,6 +652,7 @@ struct ResidentPlan {
 ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
 {
     ResidentPlan rp;
+    if (c->positions == PP_POS_GUARDED) return rp;   // per-launch kernels only
     const bool split = c->positions == PP_POS_SPLIT;
     const int64_t limit = split ? kResidentMaxNSplit
                                 : (automatic ? kResidentAutoMaxN : kResidentMaxN);
@@ -820,6 +749,76 @@ pp_status step_resident(pp_ctx *c, const ResidentPlan &rp, int64_t nsteps)
     return PP_OK;
 }
 
+// Fields of the current positions with positions mode `mode` into out (device).
+pp_status fields_with(pp_ctx *c, int mode, double *out)
+{
+    c->positions = mode;
+    void *scratch = c->stage[c->parity ^ 1];
+    pp_status st = stage_current(c, scratch, stage_kind(c));
+    if (st == PP_OK) st = force_pass(c, MODE_FIELDS, scratch, nullptr, out);
+    return st;
+}
+
+// Relative L2 difference |a - b| / |b| of two device [n][3] arrays.
+pp_status rel_diff(pp_ctx *c, const double *a, const double *b, double *parts, double *rel)
+{
+    double h[2 * kDiffBlocks];
+    PP_CUDA(launch_diff_norms(a, b, (int)(3 * c->n), parts, c->stream));
+    PP_CUDA(cudaMemcpyAsync(h, parts, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    double d2 = 0.0, b2 = 0.0;
+    for (int k = 0; k < kDiffBlocks; ++k) {
+        d2 += h[2 * k];
+        b2 += h[2 * k + 1];
+    }
+    *rel = b2 > 0 ? std::sqrt(d2 / b2) : 0.0;
+    return PP_OK;
+}
+
+// PP_POS_AUTO: the fastest staging whose fields at the current positions agree with
+// those of hi/lo staging (about 1e-7 of the FP64 result) within 5e-6 in relative L2,
+// half the 1e-5 field tolerance.  Preference order: single staging (fastest; runs on
+// the resident small-N kernel); hi/lo staging where the resident kernel can run it
+// (small N, where steps are latency-bound and resident stepping wins); guarded
+// staging (the single-staging loop with close-pair tiles summed on hi/lo parts);
+// hi/lo staging.
+pp_status decide_positions(pp_ctx *c)
+{
+    if (f64_pairs(c)) return PP_OK;   // FP64 sources: nothing to choose
+    const size_t bytes = (size_t)c->n * 3 * sizeof(double);
+    double *e_split = nullptr, *parts = nullptr;
+    if (cudaMalloc(&e_split, bytes) != cudaSuccess ||
+        cudaMalloc(&parts, 2 * kDiffBlocks * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(e_split);
+        return fail(PP_ERR_NOMEM, "cannot allocate the positions-mode check");
+    }
+    constexpr double kAutoTol = 5e-6;
+    c->auto_rel_single = c->auto_rel_guarded = NAN;
+    int chosen = PP_POS_SPLIT;
+    pp_status st = fields_with(c, PP_POS_SPLIT, e_split);
+    if (st == PP_OK) st = fields_with(c, PP_POS_SINGLE, c->aos);
+    if (st == PP_OK) st = rel_diff(c, c->aos, e_split, parts, &c->auto_rel_single);
+    if (st == PP_OK && !(c->auto_rel_single <= kAutoTol)) {
+        c->positions = PP_POS_SPLIT;
+        const bool resident_split =
+            c->resident != PP_RESIDENT_OFF && compute_resident_plan(c, true).ok;
+        if (!resident_split) {
+            st = fields_with(c, PP_POS_GUARDED, c->aos);
+            if (st == PP_OK) st = rel_diff(c, c->aos, e_split, parts, &c->auto_rel_guarded);
+            if (st == PP_OK && c->auto_rel_guarded <= kAutoTol) chosen = PP_POS_GUARDED;
+        }
+    } else if (st == PP_OK) {
+        chosen = PP_POS_SINGLE;
+    }
+    cudaFree(e_split);
+    cudaFree(parts);
+    if (st == PP_OK) st = check_device_errors(c, true);
+    c->positions = st == PP_OK ? chosen : PP_POS_SINGLE;
+    drop_graphs(c);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -835,6 +834,14 @@ const char *pp_variant_name(int index)
     int count = 0;
     const Variant *vs = variants(&count);
     return (index >= 0 && index < count) ? vs[index].name : nullptr;
+}
+
+pp_status pp_staging_check(const pp_ctx *c, double *single_rel, double *guarded_rel)
+{
+    if (!c) return fail(PP_ERR_ARG, "null context");
+    if (single_rel) *single_rel = c->auto_rel_single;
+    if (guarded_rel) *guarded_rel = c->auto_rel_guarded;
+    return PP_OK;
 }
 
 pp_status pp_get_n(const pp_ctx *c, int64_t *n)
@@ -938,7 +945,7 @@ pp_status pp_set_option(pp_ctx *c, int key, int64_t value)
         if (key == PP_OPT_ACC && (value < PP_ACC_FP64FOLD || value > PP_ACC_FP64_FULL))
             return fail(PP_ERR_ARG, "bad acc mode");
         if (key == PP_OPT_POSITIONS && value != PP_POS_SINGLE && value != PP_POS_SPLIT &&
-            value != PP_POS_AUTO)
+            value != PP_POS_AUTO && value != PP_POS_GUARDED)
             return fail(PP_ERR_ARG, "bad positions mode");
         const int new_acc = key == PP_OPT_ACC ? (int)value : c->acc;
         const bool new_auto = key == PP_OPT_POSITIONS ? value == PP_POS_AUTO : c->positions_auto;
@@ -1146,8 +1153,9 @@ pp_status pp_set_state(pp_ctx *c, const double *pos, const double *vel, const do
             return fail(PP_ERR_ARG, "invalid staging frame");
         int e = 0;
         if (std::frexp(frame[3], &e) != 0.5) return fail(PP_ERR_ARG, "frame scale must be a power of two");
-        if (frame[4] != (double)PP_POS_SINGLE && frame[4] != (double)PP_POS_SPLIT)
-            return fail(PP_ERR_ARG, "frame staging must be PP_POS_SINGLE or PP_POS_SPLIT");
+        if (frame[4] != (double)PP_POS_SINGLE && frame[4] != (double)PP_POS_SPLIT &&
+            frame[4] != (double)PP_POS_GUARDED)
+            return fail(PP_ERR_ARG, "frame staging must be PP_POS_SINGLE, _SPLIT or _GUARDED");
     }
     PP_CUDA(cudaSetDevice(c->device));
     drop_graphs(c);
@@ -1363,9 +1371,8 @@ pp_status pp_autotune(pp_ctx *c, pp_tune_result *out)
     const bool keep_resident = c->resident != PP_RESIDENT_OFF &&
                                compute_resident_plan(c, c->resident == PP_RESIDENT_AUTO).ok;
     for (int v = 0; v < count && st == PP_OK; ++v) {
-        const bool split_layout = vs[v].stage == STAGE_F32X2 || vs[v].stage == STAGE_F32IX2;
         if (vs[v].kind != (c->wts ? KIND_FORCE32W : KIND_FORCE32) || vs[v].acc != c->acc ||
-            split_layout != (c->positions == PP_POS_SPLIT))
+            vs[v].positions != c->positions)
             continue;
         if (keep_resident &&
             vs[v].stage != (c->positions == PP_POS_SPLIT ? STAGE_F32IX2 : STAGE_F32I))

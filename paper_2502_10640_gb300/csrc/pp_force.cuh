@@ -39,6 +39,9 @@ enum Mode : int {
 
 enum Acc : int { ACC_FP64FOLD = 0, ACC_KAHAN = 1, ACC_FP64FULL = 2 };
 
+// Positions modes a force kernel implements (the values of the public pp_positions).
+enum PosKind : int { POS_SINGLE = 0, POS_SPLIT = 1, POS_GUARDED = 3 };
+
 struct ForceArgs {
     const void *src;        // staged sources: float4[npad] (or double4[npad] for FP64 pair math)
     int n;                  // real particles
@@ -813,6 +816,33 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
     return d;
 }
 
+// Minimum of three floats in one instruction (sm_100+).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Guarded staging (PP_POS_GUARDED): sources and targets carry hi/lo staged
+// positions, the pair loop runs on the hi parts only (single-staging cost) and
+// keeps, per target, the smallest softened squared separation s of the tile
+// (one three-input minimum per two pairs, on the ALU pipe, while the FMA pipe
+// bounds the loop).  A tile holding a source with s < (|p_i| / 2^8)^2 is summed
+// again for that target with hi/lo separations: the single-staging error of a
+// pair term is about 3 u |p| / s^(3/2) (u = 2^-24), so every pair left to the
+// hi parts has s^(1/2) >= 2^16 u |p_i| and a relative error below about 5e-5,
+// while the few pairs close enough to spoil the sum get the ~48-bit
+// separations of split staging.  The tile that holds the CTA's own targets
+// (where the self pair, d = 0 and s = eps^2, would always pass the test) is
+// summed with hi/lo separations from the start, its lo parts read from L2.
+// Returns the squared threshold of target i.
+__device__ __forceinline__ float guard_threshold(float x, float y, float z)
+{
+    const float p2 = fmaf(z, z, fmaf(y, y, x * x));
+    return p2 * (1.0f / 65536.0f);   // (|p| / 2^8)^2
+}
+
 // Scalar loop over an interleaved tile for one target: pairs with s == 0 add
 // nothing (the fallback when a packed tile sum is not finite).
 template <int TILE, bool WEIGHTED = false, bool SPLITPOS = false>
@@ -849,16 +879,20 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
 // One tile of the packed pair loop: TILE interleaved sources, two per f32x2
 // operation, against R targets.  AX/AY/AZ receive each target's partial sums
 // over the even (low lane) and odd (high lane) sources of the tile.
-template <int R, int TILE, bool WEIGHTED, bool SPLITPOS, int UNROLL>
+// With GUARD, MS[r] receives the smallest s of target r over the tile.
+template <int R, int TILE, bool WEIGHTED, bool SPLITPOS, int UNROLL, bool GUARD = false>
 __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
                                             const float4 *__restrict__ tlo, const f2_t (&X)[R],
                                             const f2_t (&Y)[R], const f2_t (&Z)[R],
                                             const f2_t (&XL)[R], const f2_t (&YL)[R],
                                             const f2_t (&ZL)[R], f2_t EPS2, f2_t (&AX)[R],
-                                            f2_t (&AY)[R], f2_t (&AZ)[R])
+                                            f2_t (&AY)[R], f2_t (&AZ)[R], float (&MS)[R])
 {
 #pragma unroll
-    for (int r = 0; r < R; ++r) AX[r] = AY[r] = AZ[r] = 0ull;
+    for (int r = 0; r < R; ++r) {
+        AX[r] = AY[r] = AZ[r] = 0ull;
+        if (GUARD) MS[r] = 3.0e38f;
+    }
 #pragma unroll UNROLL
     for (int k = 0; k < TILE / 2; ++k) {
         const float4 a = tile[2 * k];       // x0 x1 y0 y1
@@ -886,6 +920,7 @@ __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
             const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
             float s0, s1;
             f2_unpack(S, s0, s1);
+            if (GUARD) MS[r] = fmin3(MS[r], s0, s1);
             const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
             const f2_t INV3 = WEIGHTED ? f2_mul(f2_mul(f2_mul(INV, INV), INV), WJ)
                                        : f2_mul(f2_mul(INV, INV), INV);
@@ -894,6 +929,36 @@ __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
             AZ[r] = f2_fma(INV3, DZ, AZ[r]);
         }
     }
+}
+
+// Guarded tile partial of one target (PP_POS_GUARDED): the two lanes added; if
+// the tile holds a close pair (ms < thr) or the sum is not finite (a pair with
+// s == 0), the tile is summed again for this target with hi/lo separations by
+// the scalar loop (which also skips zero-distance pairs).  tile: hi parts in
+// shared memory; glo: the same sources' lo parts in global memory; the
+// target's lo parts are read from global memory only on this rare path.
+template <int TILE, bool WEIGHTED>
+__device__ __forceinline__ float3 tile_partial_guarded(f2_t AX, f2_t AY, f2_t AZ, float ms,
+                                                       float thr, const float4 *tile,
+                                                       const float *glo, f2_t X, f2_t Y, f2_t Z,
+                                                       const float *tgt_lo, float eps2)
+{
+    float x0, x1, y0, y1, z0, z1;
+    f2_unpack(AX, x0, x1);
+    f2_unpack(AY, y0, y1);
+    f2_unpack(AZ, z0, z1);
+    float3 f = make_float3(x0 + x1, y0 + y1, z0 + z1);
+    if (ms < thr || !isfinite(f.x + f.y + f.z)) {
+        float xs, ys, zs, dummy;
+        f2_unpack(X, xs, dummy);
+        f2_unpack(Y, ys, dummy);
+        f2_unpack(Z, zs, dummy);
+        f = tile_safe1_interleaved<TILE, WEIGHTED, true>(reinterpret_cast<const float *>(tile), glo,
+                                                         xs, ys, zs, __ldcg(tgt_lo),
+                                                         __ldcg(tgt_lo + 2), __ldcg(tgt_lo + 4),
+                                                         eps2);
+    }
+    return f;
 }
 
 // Tile partial of one target: the two lanes added; a non-finite result (a pair
@@ -923,6 +988,73 @@ __device__ __forceinline__ float3 tile_partial(f2_t AX, f2_t AY, f2_t AZ, const 
     return f;
 }
 
+// One tile of guarded staging (PP_POS_GUARDED) for the R targets i0 + r T + tid
+// of a block of BI targets: the tile overlapping the block (the self pairs'
+// tile) is summed with hi/lo separations, the lo parts of its sources and
+// targets read from L2; any other tile on the hi parts, with the close-pair
+// check of tile_partial_guarded.  tile: hi parts in shared memory; glo: the lo
+// parts of the staged array (4 npad floats after its start); f: per-target
+// FP32 tile partials.
+template <int T, int R, int BI, int TILE, bool WEIGHTED, int UNROLL>
+__device__ __forceinline__ void tile_guarded(const float4 *__restrict__ tile, int jfirst, int i0,
+                                             int n, const float *__restrict__ glo,
+                                             const f2_t (&X)[R], const f2_t (&Y)[R],
+                                             const f2_t (&Z)[R], const float (&thr)[R], f2_t EPS2,
+                                             float eps2, float3 (&f)[R])
+{
+    const int tid = threadIdx.x;
+    f2_t AX[R], AY[R], AZ[R];
+    float MS[R];
+    const bool diag = jfirst < i0 + BI && i0 < jfirst + TILE;
+    if (diag) {
+        f2_t XL[R], YL[R], ZL[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r * T + tid;
+            float xl = 0.f, yl = 0.f, zl = 0.f;
+            if (i < n) {
+                const float *ql = glo + 8 * (size_t)(i >> 1) + (i & 1);
+                xl = ql[0];
+                yl = ql[2];
+                zl = ql[4];
+            }
+            XL[r] = f2_pack(xl, xl);
+            YL[r] = f2_pack(yl, yl);
+            ZL[r] = f2_pack(zl, zl);
+        }
+        const float4 *dlo = reinterpret_cast<const float4 *>(glo + 4 * (size_t)jfirst);
+        tile_packed<R, TILE, WEIGHTED, true, UNROLL>(tile, dlo, X, Y, Z, XL, YL, ZL, EPS2, AX, AY,
+                                                     AZ, MS);
+    } else {
+        tile_packed<R, TILE, WEIGHTED, false, UNROLL, true>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2,
+                                                            AX, AY, AZ, MS);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        f[r] = tile_partial_guarded<TILE, WEIGHTED>(
+            AX[r], AY[r], AZ[r], diag ? 3.0e38f : MS[r], thr[r], tile, glo + 4 * (size_t)jfirst,
+            X[r], Y[r], Z[r], glo + 8 * (size_t)(i >> 1) + (i & 1), eps2);
+    }
+}
+
+// GUARD: per-target close-pair thresholds (0 for targets past n, which sit far from
+// everything).
+template <int T, int R>
+__device__ __forceinline__ void guard_thresholds(const f2_t (&X)[R], const f2_t (&Y)[R],
+                                                 const f2_t (&Z)[R], int i0, int n,
+                                                 float (&thr)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float x, y, z, dummy;
+        f2_unpack(X[r], x, dummy);
+        f2_unpack(Y[r], y, dummy);
+        f2_unpack(Z[r], z, dummy);
+        thr[r] = i0 + r * T + (int)threadIdx.x < n ? guard_threshold(x, y, z) : 0.f;
+    }
+}
+
 // SMEM_ACC keeps the FP64 fold accumulators in shared memory (BI x 3 doubles
 // per CTA) instead of registers, trading a shared load/store per fold for
 // fewer registers and so more resident warps.
@@ -939,10 +1071,15 @@ __device__ __forceinline__ float3 tile_partial(f2_t AX, f2_t AY, f2_t AZ, const 
 // in shared memory ([hi x,y,z][lo x,y,z] x BI floats, the same bytes as the
 // FP64 accumulators).  The pair is converted to FP64 (hi + lo) once, after
 // the last tile.
+// GUARD (PP_POS_GUARDED) reads hi/lo staged sources (STAGE_F32IX2) but streams and
+// sums the hi parts only, recomputing with hi/lo separations the (target, tile)
+// partials that hold a close pair (see guard_threshold).
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false,
+          bool GUARD = false>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
+    static_assert(!(GUARD && SPLITPOS), "guarded staging streams the hi parts only");
     constexpr int BI = T * R;
     static_assert(TILE % 2 == 0, "sources are consumed in pairs");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1018,17 +1155,33 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 #pragma unroll
     for (int c = 0; c < (KAHAN && !SMEM_ACC ? 6 * R : 1); ++c) kh[c] = 0.f;
     const f2_t EPS2 = f2_pack(p.eps2f, p.eps2f);
+    // GUARD: close-pair threshold per target; the lo parts live 4 npad floats
+    // after the hi parts
+    float thr[R];
+    if (GUARD) guard_thresholds<T, R>(X, Y, Z, i0, p.n, thr);
+    const float *glo = srcf + 4 * (size_t)p.npad;
 
     int issued = 0, seen = 0;
     const bool ok = run_tiles<float4, T, TILE, STAGES, SPLITPOS>(
-        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int) {
-            f2_t AX[R], AY[R], AZ[R];
-            tile_packed<R, TILE, WEIGHTED, SPLITPOS, UNROLL>(tile, tlo, X, Y, Z, XL, YL, ZL, EPS2,
-                                                            AX, AY, AZ);
+        p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int jfirst) {
+            float3 fg[R];
+            if (GUARD) {
+                tile_guarded<T, R, BI, TILE, WEIGHTED, UNROLL>(tile, jfirst, i0, p.n, glo, X, Y, Z,
+                                                              thr, EPS2, p.eps2f, fg);
+            } else {
+                f2_t AX[R], AY[R], AZ[R];
+                float MS[R];
+                tile_packed<R, TILE, WEIGHTED, SPLITPOS, UNROLL>(tile, tlo, X, Y, Z, XL, YL, ZL,
+                                                                 EPS2, AX, AY, AZ, MS);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    fg[r] = tile_partial<TILE, WEIGHTED, SPLITPOS>(AX[r], AY[r], AZ[r], tile, tlo,
+                                                                   X[r], Y[r], Z[r], XL[r], YL[r],
+                                                                   ZL[r], p.eps2f);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const float3 f = tile_partial<TILE, WEIGHTED, SPLITPOS>(
-                    AX[r], AY[r], AZ[r], tile, tlo, X[r], Y[r], Z[r], XL[r], YL[r], ZL[r], p.eps2f);
+                const float3 f = fg[r];
                 const float fx = f.x, fy = f.y, fz = f.z;
                 if (KAHAN) {
                     const float fc[3] = {fx, fy, fz};
@@ -1094,8 +1247,8 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        finish_particle<SPLITPOS ? STAGE_F32IX2 : STAGE_F32I>(p, i0 + r * T + tid, ax64[r],
-                                                              ay64[r], az64[r]);
+        finish_particle<(SPLITPOS || GUARD) ? STAGE_F32IX2 : STAGE_F32I>(p, i0 + r * T + tid,
+                                                                         ax64[r], ay64[r], az64[r]);
 }
 
 
@@ -1162,8 +1315,9 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_cluster_kernel(const Forc
     const bool ok = run_tiles<float4, T, TILE, STAGES, false>(
         p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *, int) {
             f2_t AX[R], AY[R], AZ[R];
+            float MS[R];
             tile_packed<R, TILE, false, false, 2>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX, AY,
-                                                  AZ);
+                                                  AZ, MS);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float3 f = tile_partial<TILE, false, false>(

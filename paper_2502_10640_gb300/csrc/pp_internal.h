@@ -47,6 +47,7 @@ struct Variant {
     size_t smem;  // dynamic shared memory bytes
     int cluster;  // CTAs per thread-block cluster (0: no cluster; the j-split is then S
                   // global-partial chunks chosen by the planner, else exactly `cluster`)
+    int positions;  // PosKind
 };
 
 // One-time set-up per (device, key), e.g. a kernel's shared-memory attribute:
@@ -159,5 +160,11 @@ cudaError_t launch_moments(int pass, int n, const double *x, const double *y, co
                            const double *vx, const double *vy, const double *vz, double cx,
                            double cy, double cz, double *block_partials, double *out,
                            cudaStream_t s, const double *wts = nullptr);
+
+// Sums of |a - b|^2 and |b|^2 over n3 doubles: partials[2k], partials[2k+1] for
+// k < kDiffBlocks (a fixed reduction order; the host adds the blocks in order).
+constexpr int kDiffBlocks = 120;
+cudaError_t launch_diff_norms(const double *a, const double *b, int n3, double *partials,
+                              cudaStream_t s);
 
 }  // namespace ppk

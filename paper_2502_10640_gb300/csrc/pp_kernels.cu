@@ -14,20 +14,32 @@ Variant make_f32(const char *name)
     return Variant{name, KIND_FORCE32, ACC, SPLIT ? STAGE_F32X2 : STAGE_F32, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
                        &force_f32_kernel<T, R, TILE, STAGES, ACC, MINB, SPLIT>),
-                   (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1)};
+                   (size_t)STAGES * TILE * sizeof(float4) * (SPLIT ? 2 : 1), 0,
+                   SPLIT ? POS_SPLIT : POS_SINGLE};
 }
 
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
-          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false>
+          bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false,
+          bool GUARD = false>
 Variant make_f32x2(const char *name)
 {
     return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, KAHAN ? ACC_KAHAN : ACC_FP64FOLD,
-                   SPLITPOS ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
+                   (SPLITPOS || GUARD) ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
                        &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS,
-                                           UNROLL, KAHAN>),
+                                           UNROLL, KAHAN, GUARD>),
                    (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1) +
-                       (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0)};
+                       (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0),
+                   0, GUARD ? POS_GUARDED : SPLITPOS ? POS_SPLIT : POS_SINGLE};
+}
+
+// Guarded staging: hi/lo staged, hi parts streamed, close-pair tiles recomputed.
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
+          bool WEIGHTED = false, int UNROLL = 2, bool KAHAN = false>
+Variant make_guard(const char *name)
+{
+    return make_f32x2<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, false, UNROLL, KAHAN, true>(
+        name);
 }
 
 template <int T, int R, int TILE, int STAGES, int MINB, int CL>
@@ -36,7 +48,8 @@ Variant make_cluster(const char *name)
     return Variant{name, KIND_FORCE32, ACC_FP64FOLD, STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
                        &force_f32x2_cluster_kernel<T, R, TILE, STAGES, MINB, CL>),
-                   (size_t)STAGES * TILE * sizeof(float4) + (size_t)3 * T * R * sizeof(double), CL};
+                   (size_t)STAGES * TILE * sizeof(float4) + (size_t)3 * T * R * sizeof(double), CL,
+                   POS_SINGLE};
 }
 
 template <int T, int R, int TILE, int STAGES>
@@ -44,7 +57,7 @@ Variant make_phi(const char *name)
 {
     return Variant{name, KIND_PHI32, ACC_FP64FOLD, STAGE_F32, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(&phi_f32_kernel<T, R, TILE, STAGES>),
-                   (size_t)STAGES * TILE * sizeof(float4)};
+                   (size_t)STAGES * TILE * sizeof(float4), 0, POS_SINGLE};
 }
 
 template <int T, int R, int TILE, int STAGES>
@@ -52,7 +65,7 @@ Variant make_f64(const char *name)
 {
     return Variant{name, KIND_FORCE64, ACC_FP64FULL, STAGE_F64, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(&force_f64_kernel<T, R, TILE, STAGES>),
-                   (size_t)STAGES * TILE * sizeof(double4)};
+                   (size_t)STAGES * TILE * sizeof(double4), 0, POS_SINGLE};
 }
 
 const Variant kVariants[] = {
@@ -98,6 +111,17 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 4, true, true, true>("f32x2wsplit.sfold64.t128r2k512m4"),
     make_f32x2<128, 4, 256, 3, 4, true, true, true>("f32x2wsplit.sfold64.t128r4k256m4"),
     make_f32x2<64, 1, 128, 4, 8, false, true, true>("f32x2wsplit.fold64.t64r1k128"),
+    // guarded staging: single-precision pair loop, close-pair tiles summed with hi/lo
+    make_guard<128, 4, 1024, 2, 4, true, false, 1>("f32x2guard.sfold64.t128r4k1024s2m4u1"),
+    make_guard<128, 4, 512, 3, 4, true, false, 1>("f32x2guard.sfold64.t128r4k512m4u1"),
+    make_guard<128, 2, 128, 4, 4>("f32x2guard.fold64.t128r2k128"),
+    make_guard<64, 1, 128, 4, 8>("f32x2guard.fold64.t64r1k128"),
+    make_guard<128, 4, 512, 3, 4, true, false, 1, true>("f32x2guard.kahan.st128r4k512m4u1"),
+    make_guard<128, 2, 128, 4, 4, false, false, 2, true>("f32x2guard.kahan.t128r2k128"),
+    make_guard<64, 1, 128, 4, 8, false, false, 2, true>("f32x2guard.kahan.t64r1k128"),
+    make_guard<128, 4, 512, 3, 4, true, true>("f32x2wguard.sfold64.t128r4k512m4"),
+    make_guard<128, 2, 128, 4, 4, false, true>("f32x2wguard.fold64.t128r2k128"),
+    make_guard<64, 1, 128, 4, 8, false, true>("f32x2wguard.fold64.t64r1k128"),
     // per-particle weights (sources scaled by w_j / W)
     make_f32x2<128, 4, 512, 3, 4, true, true>("f32x2w.sfold64.t128r4k512m4"),
     make_f32x2<128, 2, 128, 4, 4, false, true>("f32x2w.fold64.t128r2k128"),

@@ -342,4 +342,45 @@ cudaError_t launch_moments(int pass, int n, const double *x, const double *y, co
     return cudaGetLastError();
 }
 
+
+// Deterministic sums of |a - b|^2 and |b|^2 over n3 doubles (one pass per block,
+// fixed tree; the host adds the kDiffBlocks block results in order).
+constexpr int kDiffThreads = 256;
+
+__global__ void __launch_bounds__(kDiffThreads)
+    diff_norms_kernel(const double *__restrict__ a, const double *__restrict__ b, int n3,
+                      double *partials)
+{
+    __shared__ double sd[kDiffThreads], sb[kDiffThreads];
+    const int chunk = (n3 + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk, hi = min(n3, lo + chunk);
+    double d2 = 0.0, b2 = 0.0;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const double d = a[k] - b[k];
+        d2 += d * d;
+        b2 += b[k] * b[k];
+    }
+    sd[threadIdx.x] = d2;
+    sb[threadIdx.x] = b2;
+    __syncthreads();
+    for (int s = kDiffThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sd[0];
+        partials[2 * blockIdx.x + 1] = sb[0];
+    }
+}
+
+cudaError_t launch_diff_norms(const double *a, const double *b, int n3, double *partials,
+                              cudaStream_t s)
+{
+    diff_norms_kernel<<<kDiffBlocks, kDiffThreads, 0, s>>>(a, b, n3, partials);
+    return cudaGetLastError();
+}
+
 }  // namespace ppk

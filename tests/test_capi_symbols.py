@@ -54,3 +54,7 @@ def test_binding_constants_match_the_header():
             "PP_POS_AUTO", "PP_ERR_STATE"} <= set(values)
     for name, value in values.items():
         assert getattr(capi, name) == int(value), name
+    defines = dict(re.findall(r"#define\s+(PP_[A-Z0-9_]+)\s+(\d+)", text))
+    assert {"PP_FRAME_LEN", "PP_FIELDS_NOALLOC_MAX_N"} <= set(defines)
+    for name, value in defines.items():
+        assert getattr(capi, name) == int(value), name

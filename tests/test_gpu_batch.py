@@ -130,6 +130,116 @@ def test_admission_by_memory_budget_and_slot_reuse():
         assert b.info()["bytes_used"] == f1
 
 
+def test_hard_ball_in_a_mix_meets_the_field_tolerance():
+    """A uniform ball of 40000 particles with softening 1e-4 R (the batched workload's
+    rule), whose closest pairs sit ~1e3 times closer than its radius, in a mix: the
+    default staging rule moves it off single staging (to guarded or hi/lo staging)
+    from its own positions, its initial accelerations (the Eq. B field of the added
+    positions) are within 1e-5 of the oracle, and it steps bitwise the same alone and
+    in the mix."""
+    n, R, w = 40000, 20e-6, 10.0
+    hard = bunch(n, "s", R, w, 1e-4, 47)
+    members = BUNCHES[:2] + [hard]
+    with capi.Batch(BIG) as b:
+        slots = [b.add(x["pos"], x["w"], x["dt"], x["eps"]) for x in members]
+        assert b.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_AUTO
+        assert b.get_option(capi.PP_OPT_POSITIONS, slots[2]) in (capi.PP_POS_GUARDED,
+                                                                  capi.PP_POS_SPLIT)
+        a0 = b.state(slots[2], n)[2]
+        b.step(4)
+        mix = b.state(slots[2], n)
+    assert rel(a0, oracle.accel(hard["pos"], w, hard["eps"])) <= TOL
+    alone = _run([hard], 4)[0]
+    for x, y in zip(alone[:3], mix[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_hi_lo_staged_batch_runs_match_oracle():
+    """Every bunch on hi/lo staging (PP_OPT_POSITIONS = PP_POS_SPLIT): 256-target blocks
+    and half-size tiles of the batch kernel, against the oracle's runs."""
+    steps = 12
+    with capi.Batch(BIG, positions=capi.PP_POS_SPLIT) as b:
+        slots = [b.add(x["pos"], x["w"], x["dt"], x["eps"]) for x in BUNCHES]
+        for s in slots:
+            assert b.get_option(capi.PP_OPT_POSITIONS, s) == capi.PP_POS_SPLIT
+        b.step(steps)
+        for x, s in zip(BUNCHES, slots):
+            p, v, a, k = b.state(s, x["n"])
+            pr, vr, ar = oracle.vv_run(x["pos"], np.zeros_like(x["pos"]), None, x["w"], x["eps"],
+                                       x["dt"], steps)
+            assert rel(p - x["pos"], pr - x["pos"]) <= TOL
+            assert rel(v, vr) <= TOL
+            assert rel(a, ar) <= TOL
+
+
+def test_guarded_batch_runs_match_oracle():
+    """Every bunch on guarded staging (PP_OPT_POSITIONS = PP_POS_GUARDED): single-staging
+    pair loop in 512-target blocks, close-pair and self-pair tiles summed with hi/lo
+    separations; against the oracle's runs."""
+    steps = 12
+    with capi.Batch(BIG, positions=capi.PP_POS_GUARDED) as b:
+        slots = [b.add(x["pos"], x["w"], x["dt"], x["eps"]) for x in BUNCHES]
+        for s in slots:
+            assert b.get_option(capi.PP_OPT_POSITIONS, s) == capi.PP_POS_GUARDED
+        b.step(steps)
+        for x, s in zip(BUNCHES, slots):
+            p, v, a, k = b.state(s, x["n"])
+            pr, vr, ar = oracle.vv_run(x["pos"], np.zeros_like(x["pos"]), None, x["w"], x["eps"],
+                                       x["dt"], steps)
+            assert rel(p - x["pos"], pr - x["pos"]) <= TOL
+            assert rel(v, vr) <= TOL
+            assert rel(a, ar) <= TOL
+
+
+def test_every_kernel_shape_gives_bitwise_the_same_results_and_the_autotuner_picks_one():
+    """The compiled shapes (threads per CTA, register budget, unrolling) change no
+    addition order, so a mix of guarded, single and hi/lo bunches steps bitwise
+    identically in each; the autotuner keeps one of them and leaves the states
+    untouched."""
+    members = BUNCHES[:3]
+    names = capi.batch_shapes()
+    assert len(names) >= 4
+    results = []
+    for k in range(len(names)):
+        with capi.Batch(BIG) as b:
+            b.set_option(capi.PP_OPT_VARIANT, k)
+            assert b.get_option(capi.PP_OPT_VARIANT) == k
+            b.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_GUARDED)
+            slots = [b.add(members[0]["pos"], members[0]["w"], members[0]["dt"],
+                           members[0]["eps"])]
+            b.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SINGLE)
+            slots.append(b.add(members[1]["pos"], members[1]["w"], members[1]["dt"],
+                               members[1]["eps"]))
+            b.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_SPLIT)
+            slots.append(b.add(members[2]["pos"], members[2]["w"], members[2]["dt"],
+                               members[2]["eps"]))
+            b.step(6)
+            results.append([b.state(s, x["n"]) for s, x in zip(slots, members)])
+    for other in results[1:]:
+        for got, ref in zip(other, results[0]):
+            for x, y in zip(got[:3], ref[:3]):
+                assert np.array_equal(x, y)
+    with capi.Batch(BIG) as b:
+        slots = [b.add(x["pos"], x["w"], x["dt"], x["eps"]) for x in members]
+        before = [b.state(s, x["n"]) for s, x in zip(slots, members)]
+        res = b.autotune()
+        assert res["candidates"] == len(names) and res["ms_per_pass"] > 0
+        assert b.get_option(capi.PP_OPT_VARIANT) == res["shape"]
+        after = [b.state(s, x["n"]) for s, x in zip(slots, members)]
+        for got, ref in zip(after, before):
+            for x, y in zip(got[:3], ref[:3]):
+                assert np.array_equal(x, y)
+        b.step(6)
+        tuned = [b.state(s, x["n"]) for s, x in zip(slots, members)]
+    with capi.Batch(BIG) as b:
+        slots = [b.add(x["pos"], x["w"], x["dt"], x["eps"]) for x in members]
+        b.step(6)
+        plain = [b.state(s, x["n"]) for s, x in zip(slots, members)]
+    for got, ref in zip(tuned, plain):
+        for x, y in zip(got[:3], ref[:3]):
+            assert np.array_equal(x, y)
+
+
 def test_batch_rejects_bad_input():
     with capi.Batch(BIG) as b:
         bad = np.zeros((10, 3))

@@ -155,16 +155,23 @@ def test_every_split_positions_variant():
                          report=f"split variant {names[v]}")
 
 
-def test_auto_positions_pick_split_staging_only_when_needed():
-    """PP_POS_AUTO: the hard ball (close pairs ~1e3 x closer than its size) switches to
-    split staging and meets 1e-5; the benchmark bunch stays on single staging."""
+def test_auto_positions_leave_single_staging_only_when_needed():
+    """PP_POS_AUTO: on the hard ball (close pairs ~1e3 x closer than its size, where
+    single staging loses ~3e-5) it takes guarded or hi/lo staging and meets 1e-5; the
+    N = 65536 Gaussian stays on single staging."""
     n, R = 40000, 20e-6
     hard = wl.uniform_sphere(n, R, seed=7 + n)
     with capi.Simulation(n, 10.0, 1e-15, 1e-9, positions=capi.PP_POS_AUTO) as sim:
         sim.load(hard)
-        assert sim.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        mode = sim.get_option(capi.PP_OPT_POSITIONS)
+        chk = sim.staging_check()
+        assert mode in (capi.PP_POS_GUARDED, capi.PP_POS_SPLIT)
+        assert chk["single_rel"] > 5e-6
+        assert (chk["guarded_rel"] <= 5e-6) == (mode == capi.PP_POS_GUARDED)
         E = sim.fields()
         sim.step(2)
+    _log(f"auto hard ball single-vs-split {chk['single_rel']:.3e} guarded-vs-split "
+         f"{chk['guarded_rel']:.3e} mode={mode}", 0.0, np.zeros(1), None)
     check_fields(E, oracle.fields(hard, 10.0, 1e-9), report="auto positions hard ball")
     b = wl.GAUSSIAN_65536
     pos = b.positions()
@@ -186,23 +193,24 @@ def test_auto_staging_is_the_default_and_travels_with_the_checkpoint():
     """PP_POS_AUTO is the default; the checkpoint frame carries the staging in force, a
     context in AUTO adopts it (bitwise resume), one with an explicit mode keeps its own,
     and a restore without a frame decides afresh."""
-    n, R, w, eps = 4099, 20e-6, 10.0, 1e-9
+    n, R, w, eps = 40000, 20e-6, 10.0, 1e-9       # single staging loses ~3e-5 here
     pos = wl.uniform_sphere(n, R, seed=7 + n)
     dt = 0.01 / math.sqrt(2 * wl.explosion_rate(n, w, R))
     with capi.Simulation(n, w, dt, eps) as a:
         assert a.get_option(capi.PP_OPT_POSITIONS_AUTO) == 1
         a.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
         a.load(pos)
-        assert a.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        mode = a.get_option(capi.PP_OPT_POSITIONS)
+        assert mode in (capi.PP_POS_GUARDED, capi.PP_POS_SPLIT)
         a.step(3)
         p, v, acc, step, frame = a.state()
-        assert len(frame) == capi.PP_FRAME_LEN and frame[4] == capi.PP_POS_SPLIT
+        assert len(frame) == capi.PP_FRAME_LEN and frame[4] == mode
         a.step(5)
         ref = a.state()
     with capi.Simulation(n, w, dt, eps) as b:
         b.set_option(capi.PP_OPT_RESIDENT, capi.PP_RESIDENT_OFF)
         b.set_state(p, v, acc, step, frame)
-        assert b.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        assert b.get_option(capi.PP_OPT_POSITIONS) == mode
         b.step(5)
         got = b.state()
     for x, y in zip(got[:3], ref[:3]):
@@ -218,7 +226,66 @@ def test_auto_staging_is_the_default_and_travels_with_the_checkpoint():
         assert e.value.status == capi.PP_ERR_ARG
     with capi.Simulation(n, w, dt, eps) as d:
         d.set_state(p, v, acc, step)
-        assert d.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
+        assert d.get_option(capi.PP_OPT_POSITIONS) in (capi.PP_POS_GUARDED, capi.PP_POS_SPLIT)
+
+
+@pytest.mark.parametrize("n,radius", HARD + [(9000, 5e-6)])
+def test_guarded_positions_on_close_pairs(n, radius):
+    """Guarded staging (single-staging pair loop, close-pair tiles summed with hi/lo
+    separations) on the hard balls: within 1e-5 of the oracle and inside the a-priori
+    bound of single staging element by element; on the largest ball, several times
+    more accurate than single staging."""
+    pos = wl.uniform_sphere(n, radius, seed=7 + n)
+    eps = 1e-9
+    ref = oracle.fields(pos, 10.0, eps)
+    E = gpu_fields(pos, 10.0, eps, positions=capi.PP_POS_GUARDED)
+    r = check_fields(E, ref, bound=bound_for(pos, 10.0, eps), report=f"guarded positions n={n}")
+    if n == 40000:
+        E1 = gpu_fields(pos, 10.0, eps, positions=capi.PP_POS_SINGLE)
+        assert 4 * r <= rel_l2(E1, ref), (r, rel_l2(E1, ref))
+
+
+def test_every_guarded_variant():
+    """Every guarded kernel (FP64 fold, compensated fold, per-particle weights) on a hard
+    ball; the context reports the variant that actually ran; steps agree with hi/lo
+    staging."""
+    n, R = 9000, 5e-6
+    pos = wl.uniform_sphere(n, R, seed=7 + n)
+    wts = 10.0 * (0.5 + wl.uniform(91, 3, n))
+    ref = oracle.fields(pos, 10.0, 1e-9)
+    ref_w = oracle.fields(pos, wts, 1e-9)
+    names = capi.variants()
+    chosen = [i for i, nm in enumerate(names) if nm.startswith(("f32x2guard.", "f32x2wguard."))]
+    assert len(chosen) >= 10
+    for v in chosen:
+        weighted = names[v].startswith("f32x2wguard.")
+        acc = capi.PP_ACC_KAHAN if ".kahan." in names[v] else capi.PP_ACC_FP64FOLD
+        with capi.Simulation(n, 10.0, 1e-15, 1e-9, acc=acc, positions=capi.PP_POS_GUARDED) as sim:
+            sim.set_option(capi.PP_OPT_VARIANT, v)
+            if weighted:
+                sim.set_weights(wts)
+            sim.load(pos)
+            E = sim.fields()
+            assert sim.get_option(capi.PP_OPT_VARIANT) == v, names[v]
+        check_fields(E, ref_w if weighted else ref, report=f"guarded variant {names[v]}")
+
+
+def test_guarded_run_matches_oracle():
+    """A softened ball stepped 40 times on guarded staging against the oracle's run."""
+    n, R, w, eps = 6000, 5e-6, 50.0, 1e-9
+    pos0 = wl.uniform_sphere(n, R, seed=36)
+    dt = 0.02 / math.sqrt(2 * wl.explosion_rate(n, w, R))
+    steps = 40
+    p_ref, v_ref, a_ref = oracle.vv_run(pos0, np.zeros_like(pos0), None, w, eps, dt, steps)
+    with capi.Simulation(n, w, dt, eps, positions=capi.PP_POS_GUARDED) as sim:
+        sim.load(pos0)
+        assert sim.get_option(capi.PP_OPT_RESIDENT_ACTIVE) == 0
+        sim.step(steps)
+        p, v, a, _, frame = sim.state()
+    assert frame[4] == capi.PP_POS_GUARDED
+    assert rel_l2(p - pos0, p_ref - pos0) <= FORCE_TOL
+    assert rel_l2(v, v_ref) <= FORCE_TOL
+    assert rel_l2(a, a_ref) <= FORCE_TOL
 
 
 def test_paper_lattice_fields():
@@ -400,7 +467,7 @@ def test_autotune_keeps_state_and_results():
         for x, y in zip(before[:3], after[:3]):
             assert np.array_equal(x, y)
         assert res["candidates"] >= 3 and res["ms_per_pass"] > 0
-        assert res["variant_name"].startswith(("f32.", "f32x2."))
+        assert res["variant_name"].startswith(("f32.", "f32x2.", "f32split.", "f32x2split."))
         E = sim.fields()
         sim.step(3)
     check_fields(E[::97], ref, report=f"autotuned {res['variant_name']} S={res['split']}")
@@ -493,8 +560,19 @@ def test_bounded_wait_reports_timeout_and_context_recovers(variant):
             sim.step(1)
         assert e.value.status == capi.PP_ERR_STATE
         sim.load(pos)
+        ref = oracle.fields(pos, 1.0, 1e-9)
+        if variant is not None:
+            # the same kernel works again: every particle inside the a-priori bound of its
+            # single staging (on this input single staging is ~3e-5 off in rel-L2, which
+            # is why the default positions mode would stage hi/lo here) ...
+            E = sim.fields()
+            assert np.all(np.linalg.norm(E - ref, axis=1) <= bound_for(pos, 1.0, 1e-9))
+            # ... and back in the default configuration the tolerance holds
+            sim.set_option(capi.PP_OPT_VARIANT, -1)
+            sim.set_option(capi.PP_OPT_POSITIONS, capi.PP_POS_AUTO)
+            sim.load(pos)
         mode = sim.get_option(capi.PP_OPT_POSITIONS)
-        check_fields(sim.fields(), oracle.fields(pos, 1.0, 1e-9),
+        check_fields(sim.fields(), ref,
                      bound=bound_for(pos, 1.0, 1e-9, split=mode == capi.PP_POS_SPLIT),
                      report=f"after timeout {variant}")
 

@@ -59,3 +59,26 @@ def test_served_results_equal_the_requests_run_alone():
             assert np.array_equal(got, want)
         d = np.linalg.norm(res.positions - ref[0]) / np.linalg.norm(ref[0])
         assert d <= 1e-5
+
+
+def test_served_trace_at_specified_sizes_against_the_oracle():
+    """Requests from the serving trace at the specified sizes (uniform spheres of 4096 to
+    524288 macro-electrons, R = 50 um, 1 nC, softening 5 nm), step counts shortened:
+    each served result's final accelerations (the Eq. B field at its final positions)
+    agree with the oracle's on 256 sampled targets within 1e-5."""
+    import oracle
+    trace = wl.serve_trace(6)
+    reqs = serve.requests_from_trace(trace, n_scale=1.0, steps_scale=0.004)
+    srv = serve.Server(150 << 30, block_steps=4)
+    try:
+        rep = srv.run(reqs)
+    finally:
+        srv.close()
+    assert rep["completed"] == len(reqs)
+    qm = -oracle.constants()["e"] / oracle.constants()["me"]
+    for res in srv.results:
+        r = reqs[res.rid]
+        idx = np.linspace(0, r.n - 1, 256).astype(np.int64)
+        ref = qm * oracle.fields_subset(res.positions, r.w, r.softening, idx)
+        err = np.linalg.norm(res.accelerations[idx] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, (r.n, err)
