@@ -40,6 +40,7 @@ FLOP_PER_PAIR = 20          # counting convention for the FP32 roofline
 WORKLOAD = wl.SPHERE_1M     # the headline: the largest single-GPU configuration
 SIDE_WORKLOAD = wl.GAUSSIAN_65536
 L2_FLUSH_BYTES = 256 * 1024 * 1024
+POSITIONS = {"auto": 2, "single": 0, "split": 1, "guarded": 3}   # pp_positions values
 
 
 def parse(argv=None):
@@ -48,6 +49,10 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere1m", choices=sorted(wl.WORKLOADS),
+                    help="the timed bunch (default: the N = 2^20 sphere; others for profiling)")
+    ap.add_argument("--positions", default="auto", choices=sorted(POSITIONS),
+                    help="staging of the timed bunch (default: the library's PP_POS_AUTO)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,8 +290,9 @@ def plan_of(sim) -> dict:
     from paper_2502_10640_gb300 import capi
     return {"kernel": capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)],
             "split": sim.get_option(capi.PP_OPT_SPLIT),
-            "positions": "hi/lo" if sim.get_option(capi.PP_OPT_POSITIONS) == capi.PP_POS_SPLIT
-            else "single",
+            "positions": {capi.PP_POS_SINGLE: "single", capi.PP_POS_SPLIT: "hi/lo",
+                          capi.PP_POS_GUARDED: "guarded"}[sim.get_option(capi.PP_OPT_POSITIONS)],
+            "staging_check": sim.staging_check(),
             "positions_chosen_by": "PP_POS_AUTO" if sim.get_option(capi.PP_OPT_POSITIONS_AUTO)
             else "explicit"}
 
@@ -392,7 +398,7 @@ def run_batched(steps: int, stream):
     with capi.Batch(150 << 30) as bt:
         bt.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
         slots = [bt.add(x.positions(), x.w, x.dt, x.eps) for x in mix]
-        n_split = sum(bt.get_option(capi.PP_OPT_POSITIONS, s) == capi.PP_POS_SPLIT for s in slots)
+        modes = [bt.get_option(capi.PP_OPT_POSITIONS, s) for s in slots]
         tune = bt.autotune()
         bt.step(2)
         torch.cuda.synchronize()
@@ -428,7 +434,9 @@ def run_batched(steps: int, stream):
             "batched": pairs / t_batch / 1e9,
             "one_bunch_per_launch": pairs / t_plain / 1e9,
             "speedup": t_plain / t_batch,
-            "bunches_on_hi_lo_staging": int(n_split),
+            "bunch_staging": {"single": modes.count(capi.PP_POS_SINGLE),
+                              "guarded": modes.count(capi.PP_POS_GUARDED),
+                              "hi/lo": modes.count(capi.PP_POS_SPLIT)},
             "batch_shape": tune["shape_name"],
             "timing": "CUDA events on the shared stream around all steps of each path "
                       "(the plain path's host gaps between its synchronous calls included)"}
@@ -436,19 +444,19 @@ def run_batched(steps: int, stream):
 
 def run_serving(count: int):
     """Bounded serving trace: Poisson arrivals at 20 requests/s of uniform-sphere runs
-    with N as specified (4096-524288) and step counts scaled by 1/20 so that the trace
+    with N as specified (4096-524288) and step counts scaled by 1/30 so that the trace
     finishes in about a minute."""
     from paper_2502_10640_gb300 import serve
     trace = wl.serve_trace(count)
-    reqs = serve.requests_from_trace(trace, n_scale=1.0, steps_scale=0.05)
+    reqs = serve.requests_from_trace(trace, n_scale=1.0, steps_scale=1.0 / 30)
     srv = serve.Server(150 << 30, block_steps=16)
     try:
         rep = srv.run(reqs)
     finally:
         srv.close()
     return {"trace": f"{count} requests, Poisson 20/s, N log-uniform 4096-524288 (as "
-                     f"specified), steps 5-250 (1/20 of 100-5000), budget 150 GB",
-            "n_scale": 1.0, "steps_scale": 0.05,
+                     f"specified), steps 3-167 (1/30 of 100-5000), budget 150 GB",
+            "n_scale": 1.0, "steps_scale": 1.0 / 30,
             "completed": rep["completed"], "p50_latency_s": rep.get("p50_latency_s"),
             "p99_latency_s": rep.get("p99_latency_s"), "pairs_per_s": rep["pairs_per_s"],
             "unit_pairs": "pair-interactions/s", "wall_s": rep["wall_s"], "blocks": rep["blocks"],
@@ -460,7 +468,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    b = WORKLOAD
+    b = wl.WORKLOADS[args.workload]
     pos = b.positions()
     n = b.n
     m = 256                                            # targets per sampled step
@@ -481,7 +489,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded cold uniform sphere)",
+        "data": f"synthetic (seeded cold {b.profile})",
         "config": bench_config(b, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -508,14 +516,15 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sms, max_mhz)
-    b = WORKLOAD
-    seed = b.seed + 1000 * rank
-    pos0 = wl.uniform_sphere(b.n, b.scale, seed)
+    b = wl.WORKLOADS[args.workload]
+    pos0 = wl.Bunch(b.name, b.n, b.w, b.eps, b.dt, b.steps, b.profile, b.scale,
+                    b.seed + 1000 * rank).positions()
     n = b.n
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    sim = capi.Simulation(n, b.w, b.dt, b.eps, tune="cache" if args.autotune else None)
+    sim = capi.Simulation(n, b.w, b.dt, b.eps, tune="cache" if args.autotune else None,
+                          positions=POSITIONS[args.positions])
     sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
     sim.load(pos0)                       # the staging decision (PP_POS_AUTO) is set-up
     if args.variant:
@@ -598,7 +607,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded cold uniform sphere)",
+        "data": f"synthetic (seeded cold {b.profile})",
         "config": bench_config(b, world),
         "precision": "FP32 pair math, FP64 per-particle fold, FP64 r/v/a",
         "plan": plan,
@@ -610,7 +619,7 @@ def run_ours(args):
     }
     line.update(extras)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, b)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
