@@ -314,7 +314,7 @@ def run_side_figure(steps: int, stream, flush, peak: float, max_mhz: float, sms:
     discipline as the headline."""
     from paper_2502_10640_gb300 import capi
     b = SIDE_WORKLOAD
-    with capi.Simulation(b.n, b.w, b.dt, b.eps, tune="cache") as sim:
+    with capi.Simulation(b.n, b.w, b.dt, b.eps) as sim:   # the library's own plan
         sim.set_option(capi.PP_OPT_STREAM, stream.cuda_stream)
         sim.load(b.positions())
         plan = plan_of(sim)

@@ -129,7 +129,7 @@ enum {
     PP_OPT_RESIDENT_ACTIVE = 9,/* pp_get_option only: 1 if pp_step now runs the resident kernel */
     PP_OPT_POSITIONS_AUTO = 10,/* pp_get_option only: 1 if PP_POS_AUTO decides the staging     */
     PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy (the
-                                  resident kernel: one grid-barrier arrival), so its bounded
+                                  resident kernel: CTA 0's first barrier arrival), so its bounded
                                   waits expire and the call returns PP_ERR_TIMEOUT (tests the
                                   timeout path; no fault, no hang) */
 };
@@ -138,20 +138,21 @@ enum {
  * steps of a pp_step call in one cooperative launch: every CTA holds the
  * whole staged source array in shared memory, computes the Eq. B sums of its
  * targets (sources split over several threads per target, FP32 partials of at
- * most 512 sources folded into FP64, the partials of a target added in a fixed
- * order) and the Eq. G/H push, then meets the other CTAs at a grid-wide
- * barrier (bounded wait: PP_ERR_TIMEOUT on expiry) before the next step.  It
- * floors s = |d|^2 + eps^2 at 1e-24 in staged units (L0^2), so the self pair
- * adds exactly 0 without a test per pair; for separations the FP32 staging
+ * most 512 sources, all partial sums compensated FP32 (TwoSum) in a fixed
+ * order, FP64 from each item's final sum on) and the Eq. G/H push, then meets
+ * the other CTAs at a grid-wide barrier, after which the next step's staged
+ * sources arrive by 1D bulk copies into shared memory (bounded waits:
+ * PP_ERR_TIMEOUT on expiry).  It floors
+ * s = |d|^2 + eps^2 at 1e-24 in staged units (L0^2), so the self pair adds
+ * exactly 0 without a test per pair; for separations the FP32 staging
  * resolves this changes s by less than one FP32 rounding.  Applicable with
- * the FP32 pair paths (PP_ACC_FP64FOLD or PP_ACC_KAHAN, whose form folds a
- * thread's tile partials into a compensated FP32 pair) and a packed-pair
- * variant (the default, or a PP_OPT_VARIANT override with interleaved
- * staging): with single staging (equal or per-particle weights) for
- * N <= 12288, with hi/lo staging (FP64 fold and equal weights; both parts in
- * shared memory) for N <= 6144.  PP_OPT_VARIANT otherwise
- * still chooses the kernel of force passes and of per-launch steps (set
- * PP_RESIDENT_OFF to step with it).
+ * the FP32 pair paths (PP_ACC_FP64FOLD or PP_ACC_KAHAN, which here fold the
+ * same way) and a packed-pair variant (the default, or a PP_OPT_VARIANT
+ * override with interleaved staging): with single staging (equal or
+ * per-particle weights) for N <= 12288, with hi/lo staging (FP64 fold and
+ * equal weights; both parts in shared memory) for N <= 6144.
+ * PP_OPT_VARIANT otherwise still chooses the kernel of force passes and of
+ * per-launch steps (set PP_RESIDENT_OFF to step with it).
  * Results differ from the per-launch kernels' at the FP32 rounding level
  * (another summation order) and are bitwise reproducible on a given device. */
 typedef enum {

@@ -513,7 +513,7 @@ class Simulation:
         self.ctx = pp_create(n, w, dt, softening)
         self.n = n
         self.acc = PP_ACC_FP64FOLD if acc is None else acc
-        self.positions = PP_POS_SINGLE if positions is None else positions
+        self.positions = PP_POS_AUTO if positions is None else positions
         self.tune = tune
         self.tuned = None
         if acc is not None:
@@ -524,7 +524,8 @@ class Simulation:
     def _apply_tuning(self):
         import json
         path = _tune_cache_path()
-        key = _tune_key(self.n, self.acc, self.positions)
+        # keyed by the staging in force (what PP_POS_AUTO decided at this load)
+        key = _tune_key(self.n, self.acc, pp_get_option(self.ctx, PP_OPT_POSITIONS))
         cache = {}
         if os.path.exists(path):
             try:

@@ -70,8 +70,8 @@ struct pp_ctx {
     int tickets_cap = 0;
     double *mom_partials = nullptr;
     double *mom_out = nullptr;
-    int *err = nullptr;            // [0]: wait ran out, [1]: non-finite input,
-                                   // [2]: grid-barrier counter of the resident kernel
+    int *err = nullptr;            // [0]: wait ran out, [1]: non-finite input
+    unsigned *res_flags = nullptr; // grid-barrier counter of the resident kernel
     double *mom_host = nullptr;    // pinned
     int *err_host = nullptr;       // pinned copy of err[0..1], read after each synchronisation
 
@@ -642,6 +642,8 @@ constexpr int64_t kResidentAutoMaxN = kResidentMaxN;
 constexpr int64_t kResidentWideN = 3072;
 // Steps per cooperative launch (bounds a launch to tens of milliseconds).
 constexpr int64_t kResidentMaxSteps = 4096;
+// Largest grid of the resident kernel (one CTA per SM).
+constexpr int kResidentMaxGrid = 256;
 
 struct ResidentPlan {
     bool ok = false;
@@ -686,12 +688,13 @@ ResidentPlan compute_resident_plan(const pp_ctx *c, bool automatic)
     }
     rp.threads = threads;
     rp.form = form;
-    // one CTA per SM at most, and at least 8 targets per CTA
+    // one CTA per SM at most, and at least 8 targets per CTA; an even number of
+    // targets per CTA keeps every CTA's staged block a whole number of source pairs
     const int64_t g0 = std::min<int64_t>((int64_t)c->sms, std::max<int64_t>(1, (c->n + 7) / 8));
-    rp.bt = (int)((c->n + g0 - 1) / g0);
+    rp.bt = (int)round_up((c->n + g0 - 1) / g0, 2);
     if (3 * rp.bt > threads) return rp;   // one thread per (component, target) item
     rp.grid = (int)((c->n + rp.bt - 1) / rp.bt);
-    if (rp.grid > c->sms * occ) return rp;
+    if (rp.grid > c->sms * occ || rp.grid > kResidentMaxGrid) return rp;
     rp.nsrc = (int)round_up(c->n, 2);
     const int qmax = threads / rp.bt;
     // at least 32 sources per thread: fewer partial sums to add at tiny N
@@ -735,12 +738,12 @@ pp_status step_resident(pp_ctx *c, const ResidentPlan &rp, int64_t nsteps)
     ra.q = rp.q;
     ra.chunk = rp.chunk;
     ra.nsrc = rp.nsrc;
-    ra.bar = reinterpret_cast<unsigned *>(c->err + 2);
+    ra.flags = c->res_flags;
     for (int64_t left = nsteps; left > 0;) {
         const int k = (int)std::min(left, kResidentMaxSteps);
         ra.parity0 = c->parity;
         ra.nsteps = k;
-        PP_CUDA(cudaMemsetAsync(ra.bar, 0, sizeof(unsigned), c->stream));
+        PP_CUDA(cudaMemsetAsync(ra.flags, 0, sizeof(unsigned), c->stream));
         PP_CUDA(launch_resident(a, ra, rp.grid, rp.threads, rp.form, c->stream));
         a.skip_copy = 0;
         c->parity ^= (k & 1);
@@ -869,6 +872,7 @@ pp_status pp_destroy(pp_ctx *c)
     cudaFree(c->mom_partials);
     cudaFree(c->mom_out);
     cudaFree(c->err);
+    cudaFree(c->res_flags);
     if (c->mom_host) cudaFreeHost(c->mom_host);
     if (c->err_host) cudaFreeHost(c->err_host);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -917,6 +921,7 @@ pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **o
                cudaMalloc(&c->mom_partials, kMomBlocks * kMomSlots * sizeof(double)) == cudaSuccess &&
                cudaMalloc(&c->mom_out, kMomSlots * sizeof(double)) == cudaSuccess &&
                cudaMalloc(&c->err, 4 * sizeof(int)) == cudaSuccess &&
+               cudaMalloc(&c->res_flags, kResidentMaxGrid * sizeof(unsigned)) == cudaSuccess &&
                cudaMallocHost(&c->mom_host, kMomSlots * sizeof(double)) == cudaSuccess &&
                cudaMallocHost(&c->err_host, 4 * sizeof(int)) == cudaSuccess;
     if (!okm) {

@@ -97,11 +97,13 @@ struct ResidentArgs {
     int q;            // threads (source chunks) per target, bt * q <= threads per CTA
     int chunk;        // sources per chunk, even
     int nsrc;         // sources summed: n rounded up to even (the odd tail is padding)
-    unsigned *bar;    // grid-barrier arrival counter, zero at launch
+    unsigned *flags;  // [0]: grid-barrier arrival counter, zero at launch
 };
 // threads per CTA: 256 or 512 (the compiled instantiations).  Forms: plain
-// (single staging, equal weights, FP64 fold), per-particle weights, hi/lo
-// staging (STAGE_F32IX2, both parts in shared memory), compensated FP32 fold.
+// (single staging, equal weights), per-particle weights, hi/lo staging
+// (STAGE_F32IX2, both parts in shared memory); the compensated-fold form runs
+// the plain kernel (the resident kernel folds compensated in every form).
+// bt (targets per CTA) is even.
 enum ResidentForm : int { RES_PLAIN = 0, RES_WEIGHTED = 1, RES_SPLIT = 2, RES_KAHAN = 3 };
 size_t resident_smem(int npad, int threads, int form);
 cudaError_t resident_configure(int npad_single, int npad_split);

@@ -1,56 +1,81 @@
 // pp_resident.cu -- small-N time stepping with every step of a pp_step call in
 // one cooperative launch: the Eq. B/E force sum and the Eq. G/H push of step
-// n+1 follow those of step n inside the same kernel, separated by a grid-wide
-// barrier, instead of one launch (and one j-split round trip through global
-// memory) per step.
+// n+1 follow those of step n inside the same kernel, instead of one launch (and
+// one j-split round trip through global memory) per step.
 //
 // At small N a step of the per-launch kernels is bound by latency, not by the
 // FP32 pipe: CTA start-up, the first bulk copy, the partial-sum publication
 // and gather, and the launch itself cost more than the 11 FP32 lane
 // operations per pair.  Here each CTA keeps the whole staged source array in
-// shared memory (loaded once per step from L2), owns BT targets, and splits
-// the sources of each target over Q threads; the Q FP64 partials of a target
-// are added in a fixed order, and the push runs one (component, target) item
-// per thread, which keeps that item's FP64 r, v, a in registers for the whole
-// launch.  The decomposition depends only on N and the SM count, so
-// results are bitwise reproducible on a given device.
+// shared memory, owns BT targets (BT even), and splits the sources of each
+// target over Q threads; the push runs one (component, target) item per
+// thread, which keeps that item's FP64 r, v, a in registers for the whole
+// launch.  The decomposition depends only on N and the SM count, so results
+// are bitwise reproducible on a given device.
+//
+// Steps are separated by a grid-wide barrier: after its push a CTA arrives on
+// one counter (release reduction); at the next step thread 0 waits (acquire
+// loads, bounded) until every CTA has arrived and then issues the copy of the
+// whole staged source array into shared memory as kResChunks 1D bulk copies
+// (TMA) on one mbarrier, which every thread waits on (bounded).  (Tried and
+// dropped: a flag per CTA with each block or group of blocks copied as soon as
+// its producer published it; the polling of ~150 flags per CTA cost more than
+// the overlap gained, 15.7 against 10.7 us per step at N = 4096.)
+//
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the sums stay
+// in compensated FP32 (TwoSum) until each (component, target) item's final
+// value: a thread's partial over its sources is an FP32 (hi, lo) pair, the Q
+// pairs of an item are added with TwoSum in a fixed order, and only the result
+// and the Eq. G/H push are FP64.
 #include "pp_internal.h"
 
 namespace ppk {
 
 namespace {
 
-constexpr int kResFold = 512;   // sources per FP32 partial before the FP64 fold
+constexpr int kResFold = 512;   // sources per FP32 partial before the compensated fold
+constexpr int kResChunks = 8;   // bulk copies per step
 // Floor on s = |d|^2 + eps^2 (staged units): the self pair (d = 0 exactly)
 // then contributes rsqrt(s)^3 * 0 = 0 without a per-pair test, and for every
 // separation the FP32 staging resolves (|d| > 1e-8 L0) the floor changes s by
 // less than one FP32 rounding.  rsqrt(1e-24)^3 = 1e36 stays finite.
 constexpr float kSelfFloor = 1e-24f;
 
-// Grid-wide barrier of a cooperative launch.  Every CTA arrives once per
-// barrier; `target` is the arrival count that completes this one.  Thread 0
-// waits at most limit_ns; the verdict is shared with the CTA.
-__device__ bool grid_sync_bounded(unsigned *bar, unsigned target, uint64_t limit_ns, bool arrive,
-                                  int *s_flag)
+// Arrive on the grid-barrier counter (release: this CTA's earlier writes, made
+// visible to thread 0 by the CTA barrier before the call, are published).
+__device__ __forceinline__ void grid_arrive(unsigned *bar)
 {
-    __syncthreads();   // the CTA's step writes happen before thread 0's release
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-        const uint64_t t0 = globaltimer_ns();
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-            if (v >= target) break;
-            if (globaltimer_ns() - t0 > limit_ns) {
-                ok = 0;
-                break;
-            }
-        }
-        *s_flag = ok;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+}
+
+// Wait (bounded) until the counter reaches target; acquire ordering on success.
+__device__ __forceinline__ bool grid_wait(const unsigned *bar, unsigned target, uint64_t limit_ns)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+    if (v >= target) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+        if (v >= target) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
-    __syncthreads();   // ... and before every thread's reads of the next step
-    return *s_flag != 0;
+}
+
+// Order this thread's generic-proxy view of memory (the acquired barrier and the
+// data it publishes) before its following async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async;" ::: "memory");
+}
+
+// hi + lo += x, compensated (TwoSum on hi, errors collected in lo).
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float x)
+{
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
 }
 
 // One component of the MODE_STEP epilogue (finish_particle, component-wise),
@@ -86,10 +111,7 @@ __device__ __forceinline__ void push_component(const ForceArgs &p, int i, int c,
 // weight ratio w_j / W (one more f32x2 multiply per two pairs).
 // SPLIT: hi/lo staged positions (STAGE_F32IX2): shared memory holds both
 // parts, and each separation is (hi_i - hi_j) + (lo_i - lo_j).
-// KAHAN (PP_ACC_KAHAN): a thread folds its FP32 tile partials into a
-// compensated FP32 pair (TwoSum) instead of FP64; the threads' pairs are
-// then added in FP64 in the fixed order, like the FP64-fold form.
-template <int NT, bool W, bool SPLIT, bool KAHAN = false>
+template <int NT, bool W, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1)
     force_resident_kernel(const ForceArgs p, const ResidentArgs ra)
 {
@@ -97,9 +119,10 @@ __global__ void __launch_bounds__(NT, 1)
     float4 *sj4 = reinterpret_cast<float4 *>(smem_raw);   // staged sources, interleaved pairs
     const float *sj = reinterpret_cast<const float *>(smem_raw);
     constexpr int NPARTS = SPLIT ? 2 : 1;                  // hi (and lo) copies, npad each
-    double *part =
-        reinterpret_cast<double *>(smem_raw + (size_t)NPARTS * p.npad * sizeof(float4));
-    __shared__ int s_flag;
+    // per-thread partial sums: [hi x, y, z][lo x, y, z] x NT floats
+    float *part = reinterpret_cast<float *>(smem_raw + (size_t)NPARTS * p.npad * sizeof(float4));
+    __shared__ uint64_t s_bar;   // completion of one step's source copies
+    __shared__ int s_abort;
 
     const int tid = threadIdx.x;
     const int tl = tid % ra.bt, qi = tid / ra.bt;
@@ -108,6 +131,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int j0 = min(qi * ra.chunk, ra.nsrc), j1 = min(j0 + ra.chunk, ra.nsrc);
     const float eps2 = fmaxf(p.eps2f, kSelfFloor);
     const f2_t EPS2 = f2_pack(eps2, eps2);
+    const int nblk = gridDim.x;
 
     // Each (component, target) item of the CTA belongs to one thread for the
     // whole launch (3 BT <= threads): that thread alone reads and writes the
@@ -126,18 +150,44 @@ __global__ void __launch_bounds__(NT, 1)
         v_o = vc[oi];
         a_o = ac[oi];
     }
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
 
     for (int s = 0; s < ra.nsteps; ++s) {
         const int par = (ra.parity0 + s) & 1;
-        // other CTAs wrote these entries during the previous step: read through L2
         const float4 *src = static_cast<const float4 *>(par ? ra.stage[1] : ra.stage[0]);
-        for (int k = tid; k < ra.nsrc; k += NT) sj4[k] = __ldcg(src + k);
-        if (SPLIT)
-            for (int k = tid; k < ra.nsrc; k += NT) sj4[p.npad + k] = __ldcg(src + p.npad + k);
+        // Copy phase: once every CTA has pushed step s - 1 (at s = 0 the sources
+        // were staged before the launch), thread 0 copies the staged array into
+        // shared memory in kResChunks bulk copies.  If the barrier wait runs out,
+        // the copies are issued all the same (of stale data; the step is void), so
+        // that the phase completes before the CTA gives up.
+        if (tid == 0) {
+            if (s > 0 && !grid_wait(ra.flags, nblk * (unsigned)s, p.timeout_ns)) {
+                s_abort = 1;
+                atomicOr(p.err, 1);
+            }
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&s_bar, 16u * (uint32_t)ra.nsrc * NPARTS);
+            const int per = (ra.nsrc / 2 + kResChunks - 1) / kResChunks * 2;   // even
+            for (int c0 = 0; c0 < ra.nsrc; c0 += per) {
+                const uint32_t bytes = 16u * (uint32_t)min(per, ra.nsrc - c0);
+                bulk_g2s(sj4 + c0, src + c0, bytes, &s_bar);
+                if (SPLIT) bulk_g2s(sj4 + p.npad + c0, src + p.npad + c0, bytes, &s_bar);
+            }
+        }
+        if (!mbar_wait_bounded(&s_bar, (uint32_t)(s & 1), p.timeout_ns)) {
+            s_abort = 1;
+            atomicOr(p.err, 1);
+            mbar_wait_bounded(&s_bar, (uint32_t)(s & 1), p.timeout_ns);   // copies in flight
+        }
         __syncthreads();
+        if (s_abort) return;   // the state is left unspecified (the call reports the timeout)
 
-        double sx = 0.0, sy = 0.0, sz = 0.0;
-        float kh[3] = {0.f, 0.f, 0.f}, kl[3] = {0.f, 0.f, 0.f};   // KAHAN: hi, lo per component
+        float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
         if (work) {
             const float *q = sj + 8 * (i >> 1) + (i & 1);
             const f2_t X = f2_pack(q[0], q[0]), Y = f2_pack(q[2], q[2]), Z = f2_pack(q[4], q[4]);
@@ -175,50 +225,39 @@ __global__ void __launch_bounds__(NT, 1)
                 f2_unpack(AX, x0, x1);
                 f2_unpack(AY, y0, y1);
                 f2_unpack(AZ, z0, z1);
-                if (KAHAN) {
-                    const float f[3] = {x0 + x1, y0 + y1, z0 + z1};
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        float hs, e;
-                        two_sum(kh[c], f[c], hs, e);
-                        kh[c] = hs;
-                        kl[c] = __fadd_rn(kl[c], e);
-                    }
-                } else {
-                    sx += (double)(x0 + x1);
-                    sy += (double)(y0 + y1);
-                    sz += (double)(z0 + z1);
-                }
-            }
-            if (KAHAN) {
-                sx = (double)kh[0] + (double)kl[0];
-                sy = (double)kh[1] + (double)kl[1];
-                sz = (double)kh[2] + (double)kl[2];
+                comp_add(hx, lx, x0 + x1);
+                comp_add(hy, ly, y0 + y1);
+                comp_add(hz, lz, z0 + z1);
             }
         }
-        part[tid] = sx;
-        part[NT + tid] = sy;
-        part[2 * NT + tid] = sz;
+        part[tid] = hx;
+        part[NT + tid] = hy;
+        part[2 * NT + tid] = hz;
+        part[3 * NT + tid] = lx;
+        part[4 * NT + tid] = ly;
+        part[5 * NT + tid] = lz;
         __syncthreads();
-        // Epilogue, one (component, target) item per thread: the FP64 pipe runs
-        // at a small fraction of the FP32 rate here, so the sums and the push are
-        // spread over as many warps (and SM sub-partitions) as there are items.
+        // Epilogue, one (component, target) item per thread: the Q partials of
+        // the item added with TwoSum in a fixed order, then FP64 for the push.
         if (owner) {
-            double sum = 0.0;
-            for (int k = 0; k < ra.q; ++k) sum += part[oc * NT + k * ra.bt + oti];   // fixed order
+            float h = 0.f, l = 0.f;
+            for (int k = 0; k < ra.q; ++k) {
+                const int t = k * ra.bt + oti;
+                comp_add(h, l, part[oc * NT + t]);
+                l = __fadd_rn(l, part[(3 + oc) * NT + t]);
+            }
+            const double sum = (double)h + (double)l;
             push_component<W, SPLIT>(p, oi, oc, occ, sum, r_o, v_o, a_o,
                                      par ? ra.stage[0] : ra.stage[1]);
         }
-        if (s + 1 < ra.nsteps || p.skip_copy) {
-            // test hook: CTA 0 withholds its first arrival, so every CTA's wait runs
-            // out (the barrier is then taken after a last step too)
-            const bool arrive = !(p.skip_copy && blockIdx.x == 0 && s == 0);
-            if (!grid_sync_bounded(ra.bar, gridDim.x * (unsigned)(s + 1), p.timeout_ns, arrive,
-                                   &s_flag)) {
-                if (tid == 0) atomicOr(p.err, 1);
-                return;   // the state is left unspecified (the call reports the timeout)
-            }
-        }
+        __syncthreads();   // every owner's staged writes of step s are done
+        // arrive for step s (test hook: CTA 0 withholds its first arrival, so every
+        // CTA's wait runs out)
+        if (tid == 0 && !(p.skip_copy && blockIdx.x == 0 && s == 0)) grid_arrive(ra.flags);
+    }
+    if (p.skip_copy && tid == 0) {
+        // test hook with a single step: wait for the last arrivals too
+        if (!grid_wait(ra.flags, nblk * (unsigned)ra.nsteps, p.timeout_ns)) atomicOr(p.err, 1);
     }
     if (owner) {
         rc[oi] = r_o;
@@ -233,8 +272,8 @@ const void *resident_fn_nt(int form)
     switch (form) {
     case RES_WEIGHTED: return reinterpret_cast<const void *>(&force_resident_kernel<NT, true, false>);
     case RES_SPLIT: return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, true>);
-    case RES_KAHAN:
-        return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false, true>);
+    case RES_KAHAN:   // the resident kernel folds compensated in every form
+        return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false>);
     default: return reinterpret_cast<const void *>(&force_resident_kernel<NT, false, false>);
     }
 }
@@ -249,7 +288,7 @@ const void *resident_fn(int threads, int form)
 size_t resident_smem(int npad, int threads, int form)
 {
     return (size_t)(form == RES_SPLIT ? 2 : 1) * npad * sizeof(float4) +
-           3 * (size_t)threads * sizeof(double);
+           6 * (size_t)threads * sizeof(float);
 }
 
 cudaError_t resident_configure(int npad_single, int npad_split)

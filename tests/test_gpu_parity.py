@@ -559,7 +559,7 @@ def test_invalid_arguments_and_states():
 def test_bounded_wait_reports_timeout_and_context_recovers(variant):
     """A withheld tile copy makes the kernel's bounded waits run out: the call returns
     PP_ERR_TIMEOUT (no fault, no hang) and the context works again after a reload.
-    Covered for the default plan (the resident kernel at this N: a withheld step
+    Covered for the default plan (the resident kernel at this N: a withheld barrier
     arrival), a scalar kernel, the shared-memory-fold packed kernel and the
     thread-block-cluster kernel (whose CTAs still meet at both cluster barriers)."""
     n = 3000

@@ -1,5 +1,5 @@
-"""Resident small-N stepping: all steps of a pp_step call in one cooperative launch with a
-grid-wide barrier between steps.  Checked against the FP64 oracle (runs of Velocity Verlet,
+"""Resident small-N stepping: all steps of a pp_step call in one cooperative launch, a
+grid-wide barrier between steps and the staged sources bulk-copied after it.  Checked against the FP64 oracle (runs of Velocity Verlet,
 Eq. G/H, on the Eq. B forces), against the per-launch kernels, for bitwise reproducibility
 (independent of how steps are grouped into calls and of checkpoints), and for its bounded
 barrier wait."""
@@ -159,10 +159,10 @@ def test_resident_split_positions_on_close_pairs(n):
 
 
 def test_resident_compensated_fold():
-    """PP_ACC_KAHAN on the resident kernel: a thread's tile partials go into a compensated
-    FP32 pair.  With one tile per thread (N = 3000) that pair is the tile partial itself,
-    so the run is bitwise the FP64-fold run; with four tiles per thread (N = 12288) both
-    stay within 1e-5 of the oracle's fields and agree with each other to 1e-12."""
+    """PP_ACC_KAHAN on the resident kernel: the resident kernel keeps all its partial sums
+    in compensated FP32 in both accumulation modes, so the runs are bitwise equal, at
+    one tile per thread (N = 3000) and at four (N = 12288), and within 1e-5 of the
+    oracle's fields."""
     n = 3000
     pos = wl.gaussian_bunch(n, 2e-6, seed=80)
     dt = dt_for(n, 2.0, 2e-6)
@@ -252,7 +252,7 @@ def test_resident_selection_rules():
 
 @pytest.mark.parametrize("steps", [1, 5])
 def test_resident_barrier_wait_reports_timeout_and_context_recovers(steps):
-    """CTA 0 withholds its first grid-barrier arrival: every CTA's bounded wait runs out,
+    """CTA 0 withholds its first barrier arrival: every CTA's bounded wait runs out,
     the call returns PP_ERR_TIMEOUT (no fault, no hang) and a reload makes the context
     usable again."""
     n = 3000
