@@ -88,9 +88,9 @@ typedef enum {
  * (lo_i - lo_j), exact in its hi part for close pairs, at six more FP32
  * operations per pair (about 30 % slower).
  * GUARDED stages hi/lo but runs the pair loop on the hi parts only, keeping
- * per target and source tile the smallest softened squared separation s (one
- * three-input minimum per two pairs, off the FP32 pipe); a tile holding a
- * source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
+ * per target and source tile the largest reciprocal softened separation
+ * rsqrt(s) (one three-input maximum per two pairs, off the FP32 pipe); a tile
+ * holding a source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
  * summed again for that target with hi/lo separations, and the tile holding
  * the target block itself always is.  Pairs left to the hi parts then carry a
  * relative error below about 5e-5 each, and the close pairs that dominate the

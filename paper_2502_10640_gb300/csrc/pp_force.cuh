@@ -816,19 +816,20 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
     return d;
 }
 
-// Minimum of three floats in one instruction (sm_100+).
-__device__ __forceinline__ float fmin3(float a, float b, float c)
+// Maximum of three floats in one instruction (sm_100+).
+__device__ __forceinline__ float fmax3(float a, float b, float c)
 {
     float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
 
 // Guarded staging (PP_POS_GUARDED): sources and targets carry hi/lo staged
 // positions, the pair loop runs on the hi parts only (single-staging cost) and
-// keeps, per target, the smallest softened squared separation s of the tile
-// (one three-input minimum per two pairs, on the ALU pipe, while the FMA pipe
-// bounds the loop).  A tile holding a source with s < (|p_i| / 2^8)^2 is summed
+// keeps, per target, the largest reciprocal softened separation rsqrt(s) of the
+// tile (one three-input maximum per two pairs over the SFU's results, on the
+// ALU pipe, while the FMA pipe bounds the loop).  A tile holding a source with
+// s < (|p_i| / 2^8)^2, i.e. rsqrt(s) > 2^8 / |p_i|, is summed
 // again for that target with hi/lo separations: the single-staging error of a
 // pair term is about 3 u |p| / s^(3/2) (u = 2^-24), so every pair left to the
 // hi parts has s^(1/2) >= 2^16 u |p_i| and a relative error below about 5e-5,
@@ -836,11 +837,11 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
 // separations of split staging.  The tile that holds the CTA's own targets
 // (where the self pair, d = 0 and s = eps^2, would always pass the test) is
 // summed with hi/lo separations from the start, its lo parts read from L2.
-// Returns the squared threshold of target i.
+// Returns target i's threshold on rsqrt(s): 2^8 / |p_i| (+inf at p_i = 0).
 __device__ __forceinline__ float guard_threshold(float x, float y, float z)
 {
     const float p2 = fmaf(z, z, fmaf(y, y, x * x));
-    return p2 * (1.0f / 65536.0f);   // (|p| / 2^8)^2
+    return 256.0f * rsqrt_sfu(p2);
 }
 
 // Scalar loop over an interleaved tile for one target: pairs with s == 0 add
@@ -879,7 +880,7 @@ __device__ __noinline__ float3 tile_safe1_interleaved(const float *__restrict__ 
 // One tile of the packed pair loop: TILE interleaved sources, two per f32x2
 // operation, against R targets.  AX/AY/AZ receive each target's partial sums
 // over the even (low lane) and odd (high lane) sources of the tile.
-// With GUARD, MS[r] receives the smallest s of target r over the tile.
+// With GUARD, MS[r] receives the largest rsqrt(s) of target r over the tile.
 template <int R, int TILE, bool WEIGHTED, bool SPLITPOS, int UNROLL, bool GUARD = false>
 __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
                                             const float4 *__restrict__ tlo, const f2_t (&X)[R],
@@ -891,7 +892,7 @@ __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         AX[r] = AY[r] = AZ[r] = 0ull;
-        if (GUARD) MS[r] = 3.0e38f;
+        if (GUARD) MS[r] = 0.f;
     }
 #pragma unroll UNROLL
     for (int k = 0; k < TILE / 2; ++k) {
@@ -920,8 +921,9 @@ __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
             const f2_t S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, EPS2)));
             float s0, s1;
             f2_unpack(S, s0, s1);
-            if (GUARD) MS[r] = fmin3(MS[r], s0, s1);
-            const f2_t INV = f2_pack(rsqrt_sfu(s0), rsqrt_sfu(s1));
+            const float q0 = rsqrt_sfu(s0), q1 = rsqrt_sfu(s1);
+            if (GUARD) MS[r] = fmax3(MS[r], q0, q1);
+            const f2_t INV = f2_pack(q0, q1);
             const f2_t INV3 = WEIGHTED ? f2_mul(f2_mul(f2_mul(INV, INV), INV), WJ)
                                        : f2_mul(f2_mul(INV, INV), INV);
             AX[r] = f2_fma(INV3, DX, AX[r]);
@@ -932,9 +934,10 @@ __device__ __forceinline__ void tile_packed(const float4 *__restrict__ tile,
 }
 
 // Guarded tile partial of one target (PP_POS_GUARDED): the two lanes added; if
-// the tile holds a close pair (ms < thr) or the sum is not finite (a pair with
-// s == 0), the tile is summed again for this target with hi/lo separations by
-// the scalar loop (which also skips zero-distance pairs).  tile: hi parts in
+// the tile holds a close pair (ms > thr, ms the largest rsqrt(s) of the tile)
+// or the sum is not finite (a pair with s == 0), the tile is summed again for
+// this target with hi/lo separations by the scalar loop (which also skips
+// zero-distance pairs).  tile: hi parts in
 // shared memory; glo: the same sources' lo parts in global memory; the
 // target's lo parts are read from global memory only on this rare path.
 template <int TILE, bool WEIGHTED>
@@ -948,7 +951,7 @@ __device__ __forceinline__ float3 tile_partial_guarded(f2_t AX, f2_t AY, f2_t AZ
     f2_unpack(AY, y0, y1);
     f2_unpack(AZ, z0, z1);
     float3 f = make_float3(x0 + x1, y0 + y1, z0 + z1);
-    if (ms < thr || !isfinite(f.x + f.y + f.z)) {
+    if (ms > thr || !isfinite(f.x + f.y + f.z)) {
         float xs, ys, zs, dummy;
         f2_unpack(X, xs, dummy);
         f2_unpack(Y, ys, dummy);
@@ -1033,7 +1036,7 @@ __device__ __forceinline__ void tile_guarded(const float4 *__restrict__ tile, in
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r * T + tid;
         f[r] = tile_partial_guarded<TILE, WEIGHTED>(
-            AX[r], AY[r], AZ[r], diag ? 3.0e38f : MS[r], thr[r], tile, glo + 4 * (size_t)jfirst,
+            AX[r], AY[r], AZ[r], diag ? 0.f : MS[r], thr[r], tile, glo + 4 * (size_t)jfirst,
             X[r], Y[r], Z[r], glo + 8 * (size_t)(i >> 1) + (i & 1), eps2);
     }
 }
@@ -1051,7 +1054,7 @@ __device__ __forceinline__ void guard_thresholds(const f2_t (&X)[R], const f2_t 
         f2_unpack(X[r], x, dummy);
         f2_unpack(Y[r], y, dummy);
         f2_unpack(Z[r], z, dummy);
-        thr[r] = i0 + r * T + (int)threadIdx.x < n ? guard_threshold(x, y, z) : 0.f;
+        thr[r] = i0 + r * T + (int)threadIdx.x < n ? guard_threshold(x, y, z) : INFINITY;
     }
 }
 
