@@ -294,7 +294,8 @@ def plan_of(sim) -> dict:
                           capi.PP_POS_GUARDED: "guarded"}[sim.get_option(capi.PP_OPT_POSITIONS)],
             "staging_check": sim.staging_check(),
             "positions_chosen_by": "PP_POS_AUTO" if sim.get_option(capi.PP_OPT_POSITIONS_AUTO)
-            else "explicit"}
+            else "explicit",
+            "launches_per_step": sim.get_option(capi.PP_OPT_LAUNCHES_PER_PASS)}
 
 
 def roofline_record(bunch, ms_per_step: float, peak: float, plan: dict, max_mhz: float,
@@ -303,7 +304,9 @@ def roofline_record(bunch, ms_per_step: float, peak: float, plan: dict, max_mhz:
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": profiled_traffic(bunch_key(bunch), plan["kernel"], plan["split"]),
-            "note": f"{FLOP_PER_PAIR} flop per pair, N^2 pairs per launch (one launch per step); "
+            "note": f"{FLOP_PER_PAIR} flop per pair, N^2 pairs per step; duration: CUDA events "
+                    f"around one step ({plan['launches_per_step']} launches: the force kernel"
+                    f"{' and the spatial sort of the tile-box guard' if plan['launches_per_step'] > 1 else ''}); "
                     f"peak = 2 x 128 FP32 lanes x {sms} SMs x {max_mhz:.0f} MHz "
                     f"({'sm_max_mhz of the measured peaks file' if peak_src == 'measured' else 'fallback clock'})"}
 
@@ -618,7 +621,7 @@ def run_ours(args):
         "plan": plan,
         "pct_fp32_peak": 100.0 * roof["frac"],
         "roofline": roof,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * plan["launches_per_step"],
         "e2e": e2e,
         "clocks": clocks.summary(),
     }

@@ -92,7 +92,13 @@ typedef enum {
  * rsqrt(s) (one three-input maximum per two pairs, off the FP32 pipe); a tile
  * holding a source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
  * summed again for that target with hi/lo separations, and the tile holding
- * the target block itself always is.  Pairs left to the hi parts then carry a
+ * the target block itself always is.  From N = 32768 on (equal weights), each
+ * force pass first sorts the staged sources along a Morton curve of their hi
+ * positions and replaces the per-pair test by one test per target and tile
+ * against the tile's bounding box: a warp sums with hi/lo separations every
+ * tile whose box comes closer than |p_i| / 256 to one of its targets (about 60
+ * more short launches per pass; the order depends on the positions alone, so
+ * results stay bitwise reproducible).  Pairs left to the hi parts then carry a
  * relative error below about 5e-5 each, and the close pairs that dominate the
  * single-staging error get split precision, at nearly single-staging speed.
  * All three work with every FP32 pair path (FP64 fold, compensated fold,
@@ -128,6 +134,9 @@ enum {
     PP_OPT_RESIDENT = 8,       /* value: a pp_resident (small-N stepping)                      */
     PP_OPT_RESIDENT_ACTIVE = 9,/* pp_get_option only: 1 if pp_step now runs the resident kernel */
     PP_OPT_POSITIONS_AUTO = 10,/* pp_get_option only: 1 if PP_POS_AUTO decides the staging     */
+    PP_OPT_LAUNCHES_PER_PASS = 11,/* pp_get_option only: kernel launches of one per-launch force
+                                  pass or step (1, or 1 + the spatial sort's with the tile-box
+                                  guard of PP_POS_GUARDED)                                   */
     PP_OPT_TEST_SKIP_COPY = 99 /* value: 1 = the next force launch withholds one tile copy (the
                                   resident kernel: CTA 0's first barrier arrival), so its bounded
                                   waits expire and the call returns PP_ERR_TIMEOUT (tests the

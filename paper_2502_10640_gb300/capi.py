@@ -39,6 +39,7 @@ PP_OPT_POSITIONS = 7
 PP_OPT_RESIDENT = 8
 PP_OPT_RESIDENT_ACTIVE = 9
 PP_OPT_POSITIONS_AUTO = 10
+PP_OPT_LAUNCHES_PER_PASS = 11
 
 PP_POS_SINGLE = 0
 PP_POS_SPLIT = 1

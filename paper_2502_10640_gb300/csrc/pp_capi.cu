@@ -72,6 +72,8 @@ struct pp_ctx {
     double *mom_out = nullptr;
     int *err = nullptr;            // [0]: wait ran out, [1]: non-finite input
     unsigned *res_flags = nullptr; // grid-barrier counter of the resident kernel
+    void *ord_ws = nullptr;        // spatial-order workspace (tile-box guard variants)
+    size_t ord_bytes = 0;
     double *mom_host = nullptr;    // pinned
     int *err_host = nullptr;       // pinned copy of err[0..1], read after each synchronisation
 
@@ -123,6 +125,13 @@ const Variant *variant_by_name(const char *want)
     std::abort();   // a missing table entry is a build error, not a runtime condition
 }
 
+// From this N on, guarded staging sorts the sources in space each pass and
+// tests tile boxes instead of every pair (measured on GB300: 372 against 397 ms
+// per step at N = 2^20, 0.58 against 0.61 ms at 32768, even at 65536); 512-source
+// tiles (hi and lo in a two-stage ring) from kBoxGuardWideN on, 256 below.
+constexpr int64_t kBoxGuardMinN = 32768;
+constexpr int64_t kBoxGuardWideN = 262144;
+
 // The variant that runs this context's force passes: the override if it fits
 // the accumulation and positions modes, else the default for N.
 const Variant *force_variant(const pp_ctx *c)
@@ -142,9 +151,13 @@ const Variant *force_variant(const pp_ctx *c)
                                        : mid ? "f32x2wguard.fold64.t128r2k128"
                                              : "f32x2wguard.fold64.t64r1k128");
         if (c->acc == PP_ACC_KAHAN)
-            return variant_by_name(big ? "f32x2guard.kahan.st128r4k512m4u1"
-                                       : mid ? "f32x2guard.kahan.t128r2k128"
-                                             : "f32x2guard.kahan.t64r1k128");
+            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.kahan.st128r4k512s2m4u1"
+                                   : big ? "f32x2guard.kahan.st128r4k512m4u1"
+                                   : mid ? "f32x2guard.kahan.t128r2k128"
+                                         : "f32x2guard.kahan.t64r1k128");
+        if (c->n >= kBoxGuardMinN)   // spatially sorted sources, one test per tile
+            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.sfold64.t128r4k512s2m4u1"
+                                                          : "f32x2bguard.sfold64.t128r4k256m4u1");
         return variant_by_name(big ? "f32x2guard.sfold64.t128r4k1024s2m4u1"
                                    : mid ? "f32x2guard.fold64.t128r2k128"
                                          : "f32x2guard.fold64.t64r1k128");
@@ -300,6 +313,20 @@ Plan make_plan(pp_ctx *c, int kind)
 
 pp_status ensure_workspace(pp_ctx *c, const Plan &pl)
 {
+    if (pl.v->order) {
+        const size_t need = order_workspace_bytes(c->npad, pl.v->tile);
+        if (need > c->ord_bytes) {
+            if (c->ord_ws) cudaFree(c->ord_ws);
+            c->ord_ws = nullptr;
+            c->ord_bytes = 0;
+            if (cudaMalloc(&c->ord_ws, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(PP_ERR_NOMEM, "cannot allocate the spatial-order workspace");
+            }
+            c->ord_bytes = need;
+            drop_graphs(c);
+        }
+    }
     const int ncomp = (pl.v->kind == KIND_PHI32) ? 1 : 3;
     const size_t need = (pl.nsplit > 1 && pl.v->cluster == 0)
                             ? (size_t)pl.nsplit * ncomp * pl.nipad * sizeof(double)
@@ -388,6 +415,23 @@ pp_status check_device_errors(pp_ctx *c, bool reset_state_on_timeout)
     return PP_OK;
 }
 
+// Launch the plan's force kernel; a variant that works on spatially sorted
+// sources first sorts a.src into the context's order workspace (sized by
+// ensure_workspace) and passes the sorted copy, permutation and tile boxes.
+cudaError_t launch_force(pp_ctx *c, const Plan &pl, ForceArgs a)
+{
+    if (pl.v->order) {
+        const OrderWork w = order_carve(c->ord_ws, c->npad, pl.v->tile);
+        const cudaError_t e =
+            launch_spatial_order(a.src, (int)c->n, c->npad, pl.v->tile, w, c->stream);
+        if (e != cudaSuccess) return e;
+        a.src = w.sorted;
+        a.perm = w.perm;
+        a.boxes = w.boxes;
+    }
+    return launch_variant(*pl.v, a, pl.grid, c->stream);
+}
+
 // One force pass over staged sources src.
 pp_status force_pass(pp_ctx *c, int mode, const void *src, void *dst, double *out)
 {
@@ -398,7 +442,7 @@ pp_status force_pass(pp_ctx *c, int mode, const void *src, void *dst, double *ou
     ForceArgs a = base_args(c, pl, mode, src, dst, out);
     a.skip_copy = c->skip_copy;
     c->skip_copy = 0;
-    PP_CUDA(launch_variant(*pl.v, a, pl.grid, c->stream));
+    PP_CUDA(launch_force(c, pl, a));
     return PP_OK;
 }
 
@@ -606,7 +650,7 @@ pp_status build_graphs(pp_ctx *c)
         cudaError_t le = cudaSuccess;
         for (int k = 0; k < c->graph_block && le == cudaSuccess; ++k) {
             ForceArgs a = base_args(c, pl, MODE_STEP, c->stage[par], c->stage[par ^ 1], nullptr);
-            le = launch_variant(*pl.v, a, pl.grid, c->stream);
+            le = launch_force(c, pl, a);
             par ^= 1;
         }
         cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
@@ -873,6 +917,7 @@ pp_status pp_destroy(pp_ctx *c)
     cudaFree(c->mom_out);
     cudaFree(c->err);
     cudaFree(c->res_flags);
+    cudaFree(c->ord_ws);
     if (c->mom_host) cudaFreeHost(c->mom_host);
     if (c->err_host) cudaFreeHost(c->err_host);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -1035,6 +1080,11 @@ pp_status pp_get_option(const pp_ctx *c, int key, int64_t *value)
         int count = 0;
         const Variant *vs = variants(&count);
         *value = (int64_t)(force_variant(c) - vs);
+        return PP_OK;
+    }
+    case PP_OPT_LAUNCHES_PER_PASS: {
+        const Variant *v = force_variant(c);
+        *value = 1 + (v->order ? order_launches(c->npad) : 0);
         return PP_OK;
     }
     default: return fail(PP_ERR_ARG, "unknown option key");

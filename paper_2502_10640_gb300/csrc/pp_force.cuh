@@ -68,6 +68,12 @@ struct ForceArgs {
     int *err;               // device error word (bit 0: a wait ran out)
     unsigned long long timeout_ns;
     int skip_copy;          // test hook: 1 = CTA 0 withholds its last tile copy, 2 = this CTA does
+    // Spatially ordered passes (tile-box guard): src is the staged array in
+    // sorted order; target k of the kernel is particle perm[k] for every
+    // epilogue read and write; boxes[2t], boxes[2t+1] are the lower and upper
+    // corners of the hi parts of sorted tile t (null: particle order).
+    const int *perm;
+    const float4 *boxes;
 };
 
 // ---- FP64 push arithmetic, written so that no multiply-add is fused: the
@@ -166,6 +172,7 @@ __device__ __forceinline__ void finish_particle(const ForceArgs &p, int i, doubl
                                                 double sz)
 {
     if (i >= p.n) return;
+    if (p.perm) i = p.perm[i];
     if (p.mode == MODE_FIELDS) {
         p.out[3 * (size_t)i + 0] = p.escale * sx;
         p.out[3 * (size_t)i + 1] = p.escale * sy;
@@ -1041,8 +1048,75 @@ __device__ __forceinline__ void tile_guarded(const float4 *__restrict__ tile, in
     }
 }
 
-// GUARD: per-target close-pair thresholds (0 for targets past n, which sit far from
-// everything).
+// Box-guarded tile (GUARD == 2, spatially sorted sources): the tile's sources
+// lie in the box [blo, bhi] (hi parts), so no pair of target r in it can have
+// rsqrt(s) above rsqrt(dbox^2 + eps^2), dbox the target's distance to the box.
+// A warp where that bound passes some target's threshold (2^8 / |p_i|), or
+// whose CTA owns the tile's targets (the self pairs), sums the tile with hi/lo
+// separations for all its targets (packed; the ring carries the lo parts of
+// the tile, the targets' lo parts are read from L2); every other warp takes
+// the hi parts only, with no test per pair.  The tile partial keeps the
+// non-finite check of tile_partial_guarded (pairs with s == 0).
+template <int T, int R, int BI, int TILE, bool WEIGHTED, int UNROLL>
+__device__ __forceinline__ void tile_boxed(const float4 *__restrict__ tile,
+                                           const float4 *__restrict__ tlo, int jfirst, int i0,
+                                           int n, const float *__restrict__ glo,
+                                           const float4 *__restrict__ box, const f2_t (&X)[R],
+                                           const f2_t (&Y)[R], const f2_t (&Z)[R],
+                                           const float (&thr)[R], f2_t EPS2, float eps2,
+                                           float3 (&f)[R])
+{
+    const int tid = threadIdx.x;
+    const float4 blo = box[0], bhi = box[1];
+    bool close = jfirst < i0 + BI && i0 < jfirst + TILE;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float x, y, z, dummy;
+        f2_unpack(X[r], x, dummy);
+        f2_unpack(Y[r], y, dummy);
+        f2_unpack(Z[r], z, dummy);
+        const float dx = fmax3(blo.x - x, x - bhi.x, 0.f);
+        const float dy = fmax3(blo.y - y, y - bhi.y, 0.f);
+        const float dz = fmax3(blo.z - z, z - bhi.z, 0.f);
+        const float sb = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        close |= rsqrt_sfu(sb) > thr[r];
+    }
+    close = __any_sync(0xffffffffu, close);
+    f2_t AX[R], AY[R], AZ[R];
+    float MS[R];
+    if (close) {
+        f2_t XL[R], YL[R], ZL[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r * T + tid;
+            float xl = 0.f, yl = 0.f, zl = 0.f;
+            if (i < n) {
+                const float *ql = glo + 8 * (size_t)(i >> 1) + (i & 1);
+                xl = ql[0];
+                yl = ql[2];
+                zl = ql[4];
+            }
+            XL[r] = f2_pack(xl, xl);
+            YL[r] = f2_pack(yl, yl);
+            ZL[r] = f2_pack(zl, zl);
+        }
+        tile_packed<R, TILE, WEIGHTED, true, UNROLL>(tile, tlo, X, Y, Z, XL, YL, ZL, EPS2, AX, AY,
+                                                     AZ, MS);
+    } else {
+        tile_packed<R, TILE, WEIGHTED, false, UNROLL>(tile, nullptr, X, Y, Z, X, Y, Z, EPS2, AX,
+                                                      AY, AZ, MS);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r * T + tid;
+        f[r] = tile_partial_guarded<TILE, WEIGHTED>(AX[r], AY[r], AZ[r], 0.f, thr[r], tile,
+                                                    glo + 4 * (size_t)jfirst, X[r], Y[r], Z[r],
+                                                    glo + 8 * (size_t)(i >> 1) + (i & 1), eps2);
+    }
+}
+
+// GUARD: per-target close-pair thresholds on rsqrt(s) (+inf for targets past n,
+// which sit far from everything).
 template <int T, int R>
 __device__ __forceinline__ void guard_thresholds(const f2_t (&X)[R], const f2_t (&Y)[R],
                                                  const f2_t (&Z)[R], int i0, int n,
@@ -1076,13 +1150,17 @@ __device__ __forceinline__ void guard_thresholds(const f2_t (&X)[R], const f2_t 
 // the last tile.
 // GUARD (PP_POS_GUARDED) reads hi/lo staged sources (STAGE_F32IX2) but streams and
 // sums the hi parts only, recomputing with hi/lo separations the (target, tile)
-// partials that hold a close pair (see guard_threshold).
+// partials that hold a close pair (see guard_threshold): GUARD == 1 finds
+// them by the largest rsqrt(s) of each tile, GUARD == 2 (spatially sorted
+// sources, p.perm and p.boxes set) by each tile's bounding box (tile_boxed).
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
           bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false,
-          bool GUARD = false>
+          int GUARD = 0>
 __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
 {
-    static_assert(!(GUARD && SPLITPOS), "guarded staging streams the hi parts only");
+    static_assert(!(GUARD != 0 && SPLITPOS), "guarded staging sums the hi parts only");
+    // the ring carries the lo parts too with hi/lo staging and with the box guard
+    constexpr bool TWO = SPLITPOS || GUARD == 2;
     constexpr int BI = T * R;
     static_assert(TILE % 2 == 0, "sources are consumed in pairs");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1098,11 +1176,11 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     const int ntiles = (j1 - j0) / TILE;
 
     float4 *ring = reinterpret_cast<float4 *>(smem_raw);
-    Ring<float4, TILE, STAGES, SPLITPOS> rg{ring, SPLITPOS ? ring + STAGES * TILE : nullptr,
+    Ring<float4, TILE, STAGES, TWO> rg{ring, TWO ? ring + STAGES * TILE : nullptr,
                                             bar_full, bar_empty};
     // FP64 accumulators in shared memory follow the tile ring(s): [3][BI]
     double *sacc = reinterpret_cast<double *>(
-        smem_raw + (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1));
+        smem_raw + (size_t)STAGES * TILE * sizeof(float4) * (TWO ? 2 : 1));
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
@@ -1161,16 +1239,20 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     // GUARD: close-pair threshold per target; the lo parts live 4 npad floats
     // after the hi parts
     float thr[R];
-    if (GUARD) guard_thresholds<T, R>(X, Y, Z, i0, p.n, thr);
+    if (GUARD != 0) guard_thresholds<T, R>(X, Y, Z, i0, p.n, thr);
     const float *glo = srcf + 4 * (size_t)p.npad;
 
     int issued = 0, seen = 0;
-    const bool ok = run_tiles<float4, T, TILE, STAGES, SPLITPOS>(
+    const bool ok = run_tiles<float4, T, TILE, STAGES, TWO>(
         p, rg, j0, ntiles, issued, seen, [&](const float4 *tile, const float4 *tlo, int jfirst) {
             float3 fg[R];
-            if (GUARD) {
+            if (GUARD == 1) {
                 tile_guarded<T, R, BI, TILE, WEIGHTED, UNROLL>(tile, jfirst, i0, p.n, glo, X, Y, Z,
                                                               thr, EPS2, p.eps2f, fg);
+            } else if (GUARD == 2) {
+                tile_boxed<T, R, BI, TILE, WEIGHTED, UNROLL>(tile, tlo, jfirst, i0, p.n, glo,
+                                                            p.boxes + 2 * (jfirst / TILE), X, Y,
+                                                            Z, thr, EPS2, p.eps2f, fg);
             } else {
                 f2_t AX[R], AY[R], AZ[R];
                 float MS[R];
@@ -1250,7 +1332,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32x2_kernel(const ForceArgs p)
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        finish_particle<(SPLITPOS || GUARD) ? STAGE_F32IX2 : STAGE_F32I>(p, i0 + r * T + tid,
+        finish_particle<(SPLITPOS || GUARD != 0) ? STAGE_F32IX2 : STAGE_F32I>(p, i0 + r * T + tid,
                                                                          ax64[r], ay64[r], az64[r]);
 }
 

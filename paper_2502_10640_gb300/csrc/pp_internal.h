@@ -48,6 +48,7 @@ struct Variant {
     int cluster;  // CTAs per thread-block cluster (0: no cluster; the j-split is then S
                   // global-partial chunks chosen by the planner, else exactly `cluster`)
     int positions;  // PosKind
+    int order = 0;  // 1: the pass sorts the staged sources in space first (tile-box guard)
 };
 
 // One-time set-up per (device, key), e.g. a kernel's shared-memory attribute:
@@ -166,6 +167,29 @@ cudaError_t launch_moments(int pass, int n, const double *x, const double *y, co
 // Sums of |a - b|^2 and |b|^2 over n3 doubles: partials[2k], partials[2k+1] for
 // k < kDiffBlocks (a fixed reduction order; the host adds the blocks in order).
 constexpr int kDiffBlocks = 120;
+// Spatial order of staged sources (tile-box guard, pp_order.cu): one device
+// workspace per context, carved into the sort keys (a power of two >= npad),
+// the sorted hi/lo copy of the staged array (STAGE_F32IX2), the tile boxes,
+// the permutation (sorted index -> particle index) and the bounding box.
+struct OrderWork {
+    unsigned long long *keys;
+    int nkeys;
+    float *sorted;
+    float4 *boxes;
+    int *perm;
+    float *bbox_part;
+    float *bbox;
+};
+int order_nkeys(int npad);
+int order_launches(int npad);   // kernel launches of launch_spatial_order
+size_t order_workspace_bytes(int npad, int tile);
+OrderWork order_carve(void *base, int npad, int tile);
+// Sorts the n staged sources of stage (STAGE_F32IX2, npad entries) along a
+// Morton curve of their hi positions (ties impossible: the index is part of the
+// key) and writes the sorted copy, permutation and boxes of tiles of `tile`.
+cudaError_t launch_spatial_order(const void *stage, int n, int npad, int tile, const OrderWork &w,
+                                 cudaStream_t s);
+
 cudaError_t launch_diff_norms(const double *a, const double *b, int n3, double *partials,
                               cudaStream_t s);
 

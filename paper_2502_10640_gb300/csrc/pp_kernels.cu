@@ -20,17 +20,18 @@ Variant make_f32(const char *name)
 
 template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
           bool WEIGHTED = false, bool SPLITPOS = false, int UNROLL = 2, bool KAHAN = false,
-          bool GUARD = false>
+          int GUARD = 0>
 Variant make_f32x2(const char *name)
 {
     return Variant{name, WEIGHTED ? KIND_FORCE32W : KIND_FORCE32, KAHAN ? ACC_KAHAN : ACC_FP64FOLD,
-                   (SPLITPOS || GUARD) ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
+                   (SPLITPOS || GUARD != 0) ? STAGE_F32IX2 : STAGE_F32I, T, R, TILE, STAGES,
                    reinterpret_cast<const void *>(
                        &force_f32x2_kernel<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, SPLITPOS,
                                            UNROLL, KAHAN, GUARD>),
-                   (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS ? 2 : 1) +
+                   (size_t)STAGES * TILE * sizeof(float4) * (SPLITPOS || GUARD == 2 ? 2 : 1) +
                        (SMEM_ACC ? (size_t)3 * T * R * sizeof(double) : 0),
-                   0, GUARD ? POS_GUARDED : SPLITPOS ? POS_SPLIT : POS_SINGLE};
+                   0, GUARD != 0 ? POS_GUARDED : SPLITPOS ? POS_SPLIT : POS_SINGLE,
+                   GUARD == 2 ? 1 : 0};
 }
 
 // Guarded staging: hi/lo staged, hi parts streamed, close-pair tiles recomputed.
@@ -38,7 +39,17 @@ template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
           bool WEIGHTED = false, int UNROLL = 2, bool KAHAN = false>
 Variant make_guard(const char *name)
 {
-    return make_f32x2<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, false, UNROLL, KAHAN, true>(
+    return make_f32x2<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, false, UNROLL, KAHAN, 1>(
+        name);
+}
+
+// Guarded staging on spatially sorted sources: close tiles found by their
+// bounding boxes (no test per pair); the ring carries hi and lo tiles.
+template <int T, int R, int TILE, int STAGES, int MINB, bool SMEM_ACC = false,
+          bool WEIGHTED = false, int UNROLL = 2, bool KAHAN = false>
+Variant make_box_guard(const char *name)
+{
+    return make_f32x2<T, R, TILE, STAGES, MINB, SMEM_ACC, WEIGHTED, false, UNROLL, KAHAN, 2>(
         name);
 }
 
@@ -119,6 +130,10 @@ const Variant kVariants[] = {
     make_guard<128, 4, 512, 3, 4, true, false, 1, true>("f32x2guard.kahan.st128r4k512m4u1"),
     make_guard<128, 2, 128, 4, 4, false, false, 2, true>("f32x2guard.kahan.t128r2k128"),
     make_guard<64, 1, 128, 4, 8, false, false, 2, true>("f32x2guard.kahan.t64r1k128"),
+    // guarded staging on spatially sorted sources (tile boxes instead of a test per pair)
+    make_box_guard<128, 4, 512, 2, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k512s2m4u1"),
+    make_box_guard<128, 4, 256, 4, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k256m4u1"),
+    make_box_guard<128, 4, 512, 2, 4, true, false, 1, true>("f32x2bguard.kahan.st128r4k512s2m4u1"),
     make_guard<128, 4, 512, 3, 4, true, true>("f32x2wguard.sfold64.t128r4k512m4"),
     make_guard<128, 2, 128, 4, 4, false, true>("f32x2wguard.fold64.t128r2k128"),
     make_guard<64, 1, 128, 4, 8, false, true>("f32x2wguard.fold64.t64r1k128"),
