@@ -92,7 +92,7 @@ typedef enum {
  * rsqrt(s) (one three-input maximum per two pairs, off the FP32 pipe); a tile
  * holding a source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
  * summed again for that target with hi/lo separations, and the tile holding
- * the target block itself always is.  From N = 32768 on (equal weights), each
+ * the target block itself always is.  From N = 32768 on, each
  * force pass first sorts the staged sources along a Morton curve of their hi
  * positions and replaces the per-pair test by one test per target and tile
  * against the tile's bounding box: a warp sums with hi/lo separations every

@@ -147,9 +147,10 @@ const Variant *force_variant(const pp_ctx *c)
     const bool big = c->n >= 32768, mid = c->n >= 8192;
     if (c->positions == PP_POS_GUARDED) {   // hi/lo staged, hi parts streamed
         if (c->wts)
-            return variant_by_name(big ? "f32x2wguard.sfold64.t128r4k512m4"
-                                       : mid ? "f32x2wguard.fold64.t128r2k128"
-                                             : "f32x2wguard.fold64.t64r1k128");
+            return variant_by_name(c->n >= kBoxGuardMinN ? "f32x2wbguard.sfold64.t128r4k512s2m4"
+                                   : big ? "f32x2wguard.sfold64.t128r4k512m4"
+                                   : mid ? "f32x2wguard.fold64.t128r2k128"
+                                         : "f32x2wguard.fold64.t64r1k128");
         if (c->acc == PP_ACC_KAHAN)
             return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.kahan.st128r4k512s2m4u1"
                                    : big ? "f32x2guard.kahan.st128r4k512m4u1"

@@ -134,6 +134,7 @@ const Variant kVariants[] = {
     make_box_guard<128, 4, 512, 2, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k512s2m4u1"),
     make_box_guard<128, 4, 256, 4, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k256m4u1"),
     make_box_guard<128, 4, 512, 2, 4, true, false, 1, true>("f32x2bguard.kahan.st128r4k512s2m4u1"),
+    make_box_guard<128, 4, 512, 2, 4, true, true>("f32x2wbguard.sfold64.t128r4k512s2m4"),
     make_guard<128, 4, 512, 3, 4, true, true>("f32x2wguard.sfold64.t128r4k512m4"),
     make_guard<128, 2, 128, 4, 4, false, true>("f32x2wguard.fold64.t128r2k128"),
     make_guard<64, 1, 128, 4, 8, false, true>("f32x2wguard.fold64.t64r1k128"),

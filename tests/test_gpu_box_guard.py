@@ -43,6 +43,13 @@ def box_variants():
     return out
 
 
+def weighted_box_variants():
+    names = capi.variants()
+    out = [i for i, nm in enumerate(names) if nm.startswith("f32x2wbguard.")]
+    assert len(out) >= 1
+    return out
+
+
 def fields_with(pos, w, eps, variant=None, acc=None, positions=GUARDED):
     with capi.Simulation(pos.shape[0], w, 1e-15, eps, acc=acc, positions=positions) as sim:
         if variant is not None:
@@ -79,6 +86,25 @@ def test_every_box_variant_matches_oracle(n):
             assert np.all(E == 0.0)
             continue
         check(E, ref, pos, 10.0, eps)
+
+
+@pytest.mark.parametrize("n", [2, 1025, 9000])
+def test_weighted_box_variant_matches_oracle(n):
+    """Per-particle weights (sources scaled by w_j / W, gathered with the positions) on the
+    sorted kernel."""
+    pos = wl.uniform_sphere(n, 5e-6, seed=400 + n)
+    wts = 10.0 * (0.5 + wl.uniform(93, 3, n))
+    eps = 1e-9
+    ref = oracle.fields(pos, wts, eps)
+    for v in weighted_box_variants():
+        with capi.Simulation(n, 10.0, 1e-15, eps, positions=GUARDED) as sim:
+            sim.set_option(capi.PP_OPT_VARIANT, v)
+            sim.set_weights(wts)
+            sim.load(pos)
+            E = sim.fields()
+            assert sim.get_option(capi.PP_OPT_VARIANT) == v
+        assert np.all(np.isfinite(E))
+        assert rel_l2(E, ref) <= FORCE_TOL
 
 
 def test_box_guard_on_the_hard_ball():
