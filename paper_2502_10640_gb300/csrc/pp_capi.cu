@@ -127,8 +127,9 @@ const Variant *variant_by_name(const char *want)
 
 // From this N on, guarded staging sorts the sources in space each pass and
 // tests tile boxes instead of every pair (measured on GB300: 372 against 397 ms
-// per step at N = 2^20, 0.58 against 0.61 ms at 32768, even at 65536); 512-source
-// tiles (hi and lo in a two-stage ring) from kBoxGuardWideN on, 256 below.
+// per step at N = 2^20, 0.55 against 0.61 ms at 32768, 1.71 against 1.75 at
+// 65536); 512-source tiles (hi and lo in a two-stage ring) from kBoxGuardWideN
+// on, 256 below; the pair loop unrolled twice (2-4 % faster than once).
 constexpr int64_t kBoxGuardMinN = 32768;
 constexpr int64_t kBoxGuardWideN = 262144;
 
@@ -152,13 +153,13 @@ const Variant *force_variant(const pp_ctx *c)
                                    : mid ? "f32x2wguard.fold64.t128r2k128"
                                          : "f32x2wguard.fold64.t64r1k128");
         if (c->acc == PP_ACC_KAHAN)
-            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.kahan.st128r4k512s2m4u1"
+            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.kahan.st128r4k512s2m4u2"
                                    : big ? "f32x2guard.kahan.st128r4k512m4u1"
                                    : mid ? "f32x2guard.kahan.t128r2k128"
                                          : "f32x2guard.kahan.t64r1k128");
         if (c->n >= kBoxGuardMinN)   // spatially sorted sources, one test per tile
-            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.sfold64.t128r4k512s2m4u1"
-                                                          : "f32x2bguard.sfold64.t128r4k256m4u1");
+            return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.sfold64.t128r4k512s2m4u2"
+                                                          : "f32x2bguard.sfold64.t128r4k256m4u2");
         return variant_by_name(big ? "f32x2guard.sfold64.t128r4k1024s2m4u1"
                                    : mid ? "f32x2guard.fold64.t128r2k128"
                                          : "f32x2guard.fold64.t64r1k128");
@@ -184,13 +185,13 @@ const Variant *force_variant(const pp_ctx *c)
         return variant_by_name("f32x2split.fold64.t64r1k128");
     }
     if (c->acc == PP_ACC_KAHAN) {  // packed pair math, compensated FP32 fold
-        if (c->n >= 32768) return variant_by_name("f32x2.kahan.st128r4k512m4u1");
+        if (c->n >= 32768) return variant_by_name("f32x2.kahan.st128r4k1024s2m4u2");
         if (c->n >= 8192) return variant_by_name("f32x2.kahan.t128r2k128");
         return variant_by_name("f32x2.kahan.t64r1k128");
     }
     // packed f32x2 pair math wherever there is enough work per CTA (defaults
     // from GB300 measurements; pp_autotune refines them per device and N)
-    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k1024s2m4u1");
+    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k1024s2m4u2");
     if (c->n >= 8192) return variant_by_name("f32x2.fold64.t128r2k128");
     return variant_by_name("f32x2.fold64.t64r1k128");
 }

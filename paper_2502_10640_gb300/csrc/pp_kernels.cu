@@ -98,11 +98,13 @@ const Variant kVariants[] = {
     make_f32x2<128, 2, 512, 3, 6, true>("f32x2.sfold64.t128r2k512m6"),
     make_f32x2<128, 4, 512, 3, 4, true, false, false, 1>("f32x2.sfold64.t128r4k512m4u1"),
     make_f32x2<128, 4, 1024, 2, 4, true, false, false, 1>("f32x2.sfold64.t128r4k1024s2m4u1"),
+    make_f32x2<128, 4, 1024, 2, 4, true, false, false, 2>("f32x2.sfold64.t128r4k1024s2m4u2"),
     make_f32x2<64, 1, 128, 4, 8>("f32x2.fold64.t64r1k128"),
     make_f32x2<64, 2, 128, 4, 8>("f32x2.fold64.t64r2k128"),
     // packed pair math, tile partials folded into compensated FP32 pairs
     make_f32x2<128, 4, 512, 3, 4, true, false, false, 1, true>("f32x2.kahan.st128r4k512m4u1"),
     make_f32x2<128, 4, 512, 3, 4, true, false, false, 2, true>("f32x2.kahan.st128r4k512m4"),
+    make_f32x2<128, 4, 1024, 2, 4, true, false, false, 2, true>("f32x2.kahan.st128r4k1024s2m4u2"),
     make_f32x2<128, 2, 128, 4, 4, false, false, false, 2, true>("f32x2.kahan.t128r2k128"),
     make_f32x2<64, 1, 128, 4, 8, false, false, false, 2, true>("f32x2.kahan.t64r1k128"),
     // j-split reduced through distributed shared memory of a thread-block cluster
@@ -132,8 +134,11 @@ const Variant kVariants[] = {
     make_guard<64, 1, 128, 4, 8, false, false, 2, true>("f32x2guard.kahan.t64r1k128"),
     // guarded staging on spatially sorted sources (tile boxes instead of a test per pair)
     make_box_guard<128, 4, 512, 2, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k512s2m4u1"),
+    make_box_guard<128, 4, 512, 2, 4, true, false, 2>("f32x2bguard.sfold64.t128r4k512s2m4u2"),
     make_box_guard<128, 4, 256, 4, 4, true, false, 1>("f32x2bguard.sfold64.t128r4k256m4u1"),
+    make_box_guard<128, 4, 256, 4, 4, true, false, 2>("f32x2bguard.sfold64.t128r4k256m4u2"),
     make_box_guard<128, 4, 512, 2, 4, true, false, 1, true>("f32x2bguard.kahan.st128r4k512s2m4u1"),
+    make_box_guard<128, 4, 512, 2, 4, true, false, 2, true>("f32x2bguard.kahan.st128r4k512s2m4u2"),
     make_box_guard<128, 4, 512, 2, 4, true, true>("f32x2wbguard.sfold64.t128r4k512s2m4"),
     make_guard<128, 4, 512, 3, 4, true, true>("f32x2wguard.sfold64.t128r4k512m4"),
     make_guard<128, 2, 128, 4, 4, false, true>("f32x2wguard.fold64.t128r2k128"),

@@ -113,7 +113,7 @@ def test_box_guard_on_the_hard_ball():
     n, R, eps = 40000, 20e-6, 1e-9
     pos = wl.uniform_sphere(n, R, seed=7 + n)
     ref = oracle.fields(pos, 10.0, eps)
-    v = capi.variants().index("f32x2bguard.sfold64.t128r4k512s2m4u1")
+    v = capi.variants().index("f32x2bguard.sfold64.t128r4k512s2m4u2")
     E = fields_with(pos, 10.0, eps, variant=v)
     idx = np.linspace(0, n - 1, 4096).astype(np.int64)
     r = rel_l2(E, ref)
@@ -188,7 +188,7 @@ def test_box_guard_run_matches_oracle():
     dt = 0.02 / math.sqrt(2 * wl.explosion_rate(n, w, R))
     steps = 40
     p_ref, v_ref, a_ref = oracle.vv_run(pos0, np.zeros_like(pos0), None, w, eps, dt, steps)
-    v = capi.variants().index("f32x2bguard.sfold64.t128r4k512s2m4u1")
+    v = capi.variants().index("f32x2bguard.sfold64.t128r4k512s2m4u2")
     with capi.Simulation(n, w, dt, eps, positions=GUARDED) as sim:
         sim.set_option(capi.PP_OPT_VARIANT, v)
         sim.load(pos0)
