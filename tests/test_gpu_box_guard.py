@@ -198,3 +198,53 @@ def test_box_guard_run_matches_oracle():
     assert rel_l2(p - pos0, p_ref - pos0) <= FORCE_TOL
     assert rel_l2(vel, v_ref) <= FORCE_TOL
     assert rel_l2(a, a_ref) <= FORCE_TOL
+
+
+def sort_launches(npad):
+    """Launches of one spatial sort: bounding box (2), keys, the shared-memory sort of
+    2048-key blocks, then per merge size k above 2048 one global step per j >= 2048 and
+    one shared-memory pass; gather and tile boxes."""
+    nkeys = 2
+    while nkeys < npad:
+        nkeys *= 2
+    L = min(nkeys, 2048)
+    count, k = 6, 2 * L
+    while k <= nkeys:
+        count += int(math.log2(k // L)) + 1
+        k *= 2
+    return count
+
+
+@pytest.mark.parametrize("n,mode,sorted_", [(1 << 20, GUARDED, True), (32768, GUARDED, True),
+                                             (20000, GUARDED, False),
+                                             (1 << 20, capi.PP_POS_SINGLE, False)])
+def test_launches_per_pass(n, mode, sorted_):
+    """PP_OPT_LAUNCHES_PER_PASS: the force launch, plus the sort's launches where the plan
+    sorts (the bench multiplies it by the timed steps)."""
+    with capi.Simulation(n, 1.0, 1e-15, 0.0, positions=mode) as sim:
+        got = sim.get_option(capi.PP_OPT_LAUNCHES_PER_PASS)
+        name = capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)]
+    assert name.startswith(("f32x2bguard.", "f32x2wbguard.")) == sorted_, name
+    assert got == (1 + sort_launches(n) if sorted_ else 1), (got, name)
+    if n == 1 << 20 and sorted_:
+        assert got == 61
+
+
+def test_autotune_under_guarded_staging():
+    """The autotuner times the sorted variants with their sort included; its choice keeps
+    the state and meets the tolerance on the hard ball."""
+    n, R, eps = 40000, 20e-6, 1e-9
+    pos = wl.uniform_sphere(n, R, seed=7 + n)
+    idx = np.arange(0, n, 37)
+    ref = oracle.fields_subset(pos, 10.0, eps, idx)
+    with capi.Simulation(n, 10.0, 1e-15, eps, positions=GUARDED) as sim:
+        sim.load(pos)
+        before = sim.state()
+        res = sim.autotune()
+        after = sim.state()
+        for x, y in zip(before[:3], after[:3]):
+            assert np.array_equal(x, y)
+        assert res["variant_name"].startswith(("f32x2guard.", "f32x2bguard.")), res
+        assert res["candidates"] >= 4
+        E = sim.fields()
+    assert rel_l2(E[idx], ref) <= FORCE_TOL

@@ -485,7 +485,7 @@ def test_autotune_keeps_state_and_results():
         mode = sim.get_option(capi.PP_OPT_POSITIONS)
         prefix = {capi.PP_POS_SINGLE: ("f32.", "f32x2.", "f32x2cl"),
                   capi.PP_POS_SPLIT: ("f32split.", "f32x2split."),
-                  capi.PP_POS_GUARDED: ("f32x2guard.",)}[mode]
+                  capi.PP_POS_GUARDED: ("f32x2guard.", "f32x2bguard.")}[mode]
         assert res["variant_name"].startswith(prefix), (mode, res["variant_name"])
         E = sim.fields()
         sim.step(3)
