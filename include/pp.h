@@ -174,9 +174,12 @@ typedef enum {
 /*
  * Create a context for N macro-electrons of common weight w (Sec. 2.1 assumes
  * one weight for all macro-particles), time step dt > 0 and softening
- * eps >= 0 (metres).  Allocates device memory on the current CUDA device.
- * N >= 1 (N = 0 -> PP_ERR_ARG); N <= 2^28.  On success *out receives the
- * context; on failure *out is set to NULL.
+ * eps >= 0 (metres).  Allocates the state and staging buffers on the current
+ * CUDA device; force passes allocate their workspaces on first use (the j-split
+ * partial sums; with guarded staging from N = 32768 on, the spatial-order
+ * workspace, 44 to 52 bytes per particle) and return PP_ERR_NOMEM if that
+ * fails.  N >= 1 (N = 0 -> PP_ERR_ARG); N <= 2^28.  On success *out receives
+ * the context; on failure *out is set to NULL.
  */
 pp_status pp_create(int64_t N, double w, double dt, double softening, pp_ctx **out);
 
