@@ -613,7 +613,10 @@ def run_ours(args):
     roof = roofline_record(b, per_step_ms, peak, plan, max_mhz, sms, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": per_step_ms,
+        "step_ms": {"median": float(np.median(ms)), "min": float(min(ms)), "max": float(max(ms)),
+                    "timing": "CUDA events around each timed step (this rank)"},
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": f"synthetic (seeded cold {b.profile})",
         "config": bench_config(b, world),
