@@ -92,7 +92,7 @@ typedef enum {
  * rsqrt(s) (one three-input maximum per two pairs, off the FP32 pipe); a tile
  * holding a source with s < (|p_i| / 256)^2 (p_i: the target's staged position) is
  * summed again for that target with hi/lo separations, and the tile holding
- * the target block itself always is.  From N = 32768 on, each
+ * the target block itself always is.  From N = 98304 on, each
  * force pass first sorts the staged sources along a Morton curve of their hi
  * positions and replaces the per-pair test by one test per target and tile
  * against the tile's bounding box: a warp sums with hi/lo separations every
@@ -176,7 +176,7 @@ typedef enum {
  * one weight for all macro-particles), time step dt > 0 and softening
  * eps >= 0 (metres).  Allocates the state and staging buffers on the current
  * CUDA device; force passes allocate their workspaces on first use (the j-split
- * partial sums; with guarded staging from N = 32768 on, the spatial-order
+ * partial sums; with guarded staging from N = 98304 on, the spatial-order
  * workspace, 44 to 52 bytes per particle) and return PP_ERR_NOMEM if that
  * fails.  N >= 1 (N = 0 -> PP_ERR_ARG); N <= 2^28.  On success *out receives
  * the context; on failure *out is set to NULL.

@@ -126,12 +126,16 @@ const Variant *variant_by_name(const char *want)
 }
 
 // From this N on, guarded staging sorts the sources in space each pass and
-// tests tile boxes instead of every pair (measured on GB300: 372 against 397 ms
-// per step at N = 2^20, 0.55 against 0.61 ms at 32768, 1.71 against 1.75 at
-// 65536); 512-source tiles (hi and lo in a two-stage ring) from kBoxGuardWideN
-// on, 256 below; the pair loop unrolled twice (2-4 % faster than once).
-constexpr int64_t kBoxGuardMinN = 32768;
-constexpr int64_t kBoxGuardWideN = 262144;
+// tests tile boxes instead of every pair.  Measured on GB300 (ms per step, the
+// fastest box form against the fastest per-pair form, uniform balls and
+// Gaussians alike): 3.61 against 3.75 at N = 98304, 6.21 against 6.50 at
+// 131072, 23.6 against 24.9 at 262144, 366 against 397 at 2^20; below 98304
+// the per-pair test wins (1.67 against 1.75 at 65536, 0.45 against 0.58 at
+// 32768), its small tiles filling the GPU better.  512-source box tiles (hi
+// and lo in a two-stage ring) from kBoxGuardWideN on, 256 below; the pair loop
+// unrolled twice (2-4 % faster than once).
+constexpr int64_t kBoxGuardMinN = 98304;
+constexpr int64_t kBoxGuardWideN = 196608;
 
 // The variant that runs this context's force passes: the override if it fits
 // the accumulation and positions modes, else the default for N.
@@ -160,9 +164,8 @@ const Variant *force_variant(const pp_ctx *c)
         if (c->n >= kBoxGuardMinN)   // spatially sorted sources, one test per tile
             return variant_by_name(c->n >= kBoxGuardWideN ? "f32x2bguard.sfold64.t128r4k512s2m4u2"
                                                           : "f32x2bguard.sfold64.t128r4k256m4u2");
-        return variant_by_name(big ? "f32x2guard.sfold64.t128r4k1024s2m4u1"
-                                   : mid ? "f32x2guard.fold64.t128r2k128"
-                                         : "f32x2guard.fold64.t64r1k128");
+        return variant_by_name(c->n >= 49152 ? "f32x2guard.fold64.t128r2k128"
+                                             : "f32x2guard.fold64.t64r1k128");
     }
     if (c->wts && c->positions == PP_POS_SPLIT) {  // weights on hi/lo staged sources
         if (c->n >= 32768) return variant_by_name("f32x2wsplit.sfold64.t128r2k512m4");
@@ -189,10 +192,13 @@ const Variant *force_variant(const pp_ctx *c)
         if (c->n >= 8192) return variant_by_name("f32x2.kahan.t128r2k128");
         return variant_by_name("f32x2.kahan.t64r1k128");
     }
-    // packed f32x2 pair math wherever there is enough work per CTA (defaults
-    // from GB300 measurements; pp_autotune refines them per device and N)
-    if (c->n >= 32768) return variant_by_name("f32x2.sfold64.t128r4k1024s2m4u2");
-    if (c->n >= 8192) return variant_by_name("f32x2.fold64.t128r2k128");
+    // packed f32x2 pair math; defaults from GB300 measurements (ms per step at
+    // N = 8192 / 32768 / 98304 / 262144: 0.039 / 0.410 / 3.36 / 22.5 for the
+    // chosen forms against 0.047 / 0.458 / 3.49 / 23.1 for the next best);
+    // pp_autotune refines them per device and N
+    if (c->n >= 196608) return variant_by_name("f32x2.sfold64.t128r4k1024s2m4u2");
+    if (c->n >= 49152) return variant_by_name("f32x2.sfold64.t128r2k512m6");
+    if (c->n >= 12288) return variant_by_name("f32x2.fold64.t128r2k128");
     return variant_by_name("f32x2.fold64.t64r1k128");
 }
 

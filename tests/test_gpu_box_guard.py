@@ -215,7 +215,7 @@ def sort_launches(npad):
     return count
 
 
-@pytest.mark.parametrize("n,mode,sorted_", [(1 << 20, GUARDED, True), (32768, GUARDED, True),
+@pytest.mark.parametrize("n,mode,sorted_", [(1 << 20, GUARDED, True), (131072, GUARDED, True), (65536, GUARDED, False),
                                              (20000, GUARDED, False),
                                              (1 << 20, capi.PP_POS_SINGLE, False)])
 def test_launches_per_pass(n, mode, sorted_):
