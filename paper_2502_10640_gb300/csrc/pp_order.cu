@@ -18,8 +18,8 @@
 //      layout) and the permutation sorted index -> particle index;
 //   5. the box of each tile of the sorted copy (hi parts, real sources only).
 //
-// The sort costs about 55 launches and a few tens of megabytes of traffic at
-// N = 2^20, well under 1 % of a step of the O(N^2) pass it serves.
+// The whole order costs 60 launches and about 0.5 ms at N = 2^20 (measured on
+// GB300), 0.13 % of a step of the O(N^2) pass it serves.
 #include <cfloat>
 
 #include "pp_internal.h"
