@@ -136,7 +136,7 @@ def test_coincident_sources_and_no_softening():
 
 
 def test_large_n_default_plan_sorts_and_matches_sampled_oracle():
-    """From N = 131072 on guarded staging takes the sorted tile-box kernel by default;
+    """At N = 131072 guarded staging takes the sorted tile-box kernel by default;
     sampled targets against the oracle, and the same fields bitwise on a second run."""
     n, R, eps = 131072, 50e-6, 5e-9
     pos = wl.uniform_sphere(n, R, seed=123)
@@ -248,3 +248,21 @@ def test_autotune_under_guarded_staging():
         assert res["candidates"] >= 4
         E = sim.fields()
     assert rel_l2(E[idx], ref) <= FORCE_TOL
+
+
+def test_box_guard_just_above_a_power_of_two():
+    """N = 131073: the sort pads its keys to 262144, the staged array to the next tile;
+    sampled targets (the first and last particles included) against the oracle."""
+    n, R, eps = 131073, 50e-6, 5e-9
+    pos = wl.uniform_sphere(n, R, seed=125)
+    with capi.Simulation(n, 1.0, 1e-15, eps, positions=GUARDED) as sim:
+        sim.load(pos)
+        assert capi.variants()[sim.get_option(capi.PP_OPT_VARIANT)].startswith("f32x2bguard.")
+        E = sim.fields()
+    idx = np.unique(np.concatenate([np.linspace(0, n - 1, 1024).astype(np.int64),
+                                    np.arange(n - 8, n)]))
+    ref = oracle.fields_subset(pos, 1.0, eps, idx)
+    assert np.all(np.isfinite(E))
+    assert rel_l2(E[idx], ref) <= FORCE_TOL
+    bound = field_error_bound(pos, 1.0, eps, idx, K_E)
+    assert float(np.max(np.linalg.norm(E[idx] - ref, axis=1) / bound)) <= 1.0
